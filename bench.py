@@ -1,0 +1,452 @@
+#!/usr/bin/env python3
+"""Throughput of the SE1P evaluation (phi + force + energy) on one GB300.
+
+Workload (default): N = 100 000 uniform charges in L = [1,1,1] (z periodic),
+charges U[-1,1] shifted to zero net charge, xi = 20, M = 64^3, P = 24,
+s_l = 2 on |k3| <= 4 (n_l = 4), s0 ~ 2 sqrt 2 (n0 = 288), rc = 0.15; mixed
+FP32/FP64 precision.  One step = one full se1p_eval (pack, gridding, AFT,
+scaling, AIFT, gathering, real space, energy) over the resident batch.
+
+Prints one JSON line.  `--impl reference` times the FP64 oracle (direct
+Ewald1P sums) on the host cores on a bounded sample of the same workload.
+With torchrun (N > 1) every rank evaluates its own replica (no data-path
+collective); rank 0 prints the whole-job rate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particles/sec (phi+force) at rms rel err 1e-6, mixed vs FP64 GPU; % HBM roofline"
+UNIT = "particles/s"
+L2_BYTES = 129 * 1024 * 1024
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="se1p", choices=["se1p", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="only warm-up + timed steps (for ncu launch lists); prints a short line")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_1611_09538_gb300 import inputs
+    return {"c1": inputs.config_c1, "c2": inputs.config_c2, "c3": inputs.config_c3}[name]()
+
+
+def workload_config(sys_, name, precision):
+    p = sys_.params
+    return {
+        "workload": f"{name.upper()}: N={len(sys_.q)} uniform charges, L={list(sys_.L)}, xi={p['xi']}, "
+                    f"M={list(p['M'])}, P={p['P']}, Mt={p['Mt']}, n0={p['n0']}, nI={p['nI']}, nl={p['nl']}, "
+                    f"rc={p['rc']}",
+        "N": len(sys_.q), "precision": precision, "L2": "flushed between timed steps (256 MiB write)",
+    }
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        self.t0 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], None, set()
+        for line in out.splitlines():
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(sys_, budget_s, targets_hint=None):
+    """Time the direct Ewald1P oracle on a bounded set of targets (against all N sources)."""
+    from oracle import direct
+    direct.build()
+    p = sys_.params
+    rng = np.random.default_rng(1234)
+    n = len(sys_.q)
+    t0 = time.perf_counter()
+    first = rng.choice(n, size=2, replace=False)
+    pp, ff = direct.ewald1p_parts(sys_.x, sys_.q, sys_.L[2], p["xi"], p["rc"], targets=first)
+    dt = time.perf_counter() - t0
+    per = dt / 2
+    extra = max(0, min(64, int(budget_s / max(per, 1e-9)) - 2)) if targets_hint is None else targets_hint
+    tg = first
+    if extra > 0:
+        more = rng.choice(np.setdiff1d(np.arange(n), first), size=extra, replace=False)
+        t1 = time.perf_counter()
+        pp2, ff2 = direct.ewald1p_parts(sys_.x, sys_.q, sys_.L[2], p["xi"], p["rc"], targets=more)
+        dt += time.perf_counter() - t1
+        tg = np.concatenate([first, more])
+        pp = np.concatenate([pp, pp2])
+        ff = np.concatenate([ff, ff2])
+    return {
+        "targets": tg, "phi": pp.sum(axis=1), "F": ff.sum(axis=1), "seconds": dt,
+        "rate": len(tg) / dt, "cores": direct.num_threads(),
+    }
+
+
+def rel_rms(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2)))
+
+
+# ------------------------------------------------------------------ roofline bookkeeping
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1611_09538_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel, workload_name):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = t.get(f"{kernel}@{workload_name}")
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def roofline(stage_ms, n_evals, info, n, precision, peaks, clock_mhz, workload_name):
+    """Roofline of the dominant stage (largest share of the step)."""
+    P = info["P"]
+    per = {k: v / max(n_evals, 1) for k, v in stage_ms.items()}
+    dom = max(per, key=per.get)
+    lanes = NUM_SMS * FP32_LANES_PER_SM
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = lanes * 2 * mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
+    # FP64 (non-tensor) rate of this part: 1.25 TFLOP/s nominal (64x below FP32)
+    fp64_peak = 1.25
+    peak_alu = fp32_peak if precision == "mixed" else fp64_peak
+    t = per[dom] * 1e-3
+    word = 4 if precision == "mixed" else 8
+    grid_pts = info["M3"] * info["Mt"] * info["Mt"]
+    if dom == "gather":
+        flops = n * 4.0 * P ** 3  # two FMA per support point: phi and the x-derivative chain
+        return dict(kernel="k_gather", bound="alu", achieved=flops / t / 1e12, peak=peak_alu, unit="TFLOP/s",
+                    frac=flops / t / 1e12 / peak_alu, traffic=committed_traffic("k_gather", workload_name),
+                    algorithmic=f"{4 * P ** 3} flop/particle", stage_ms=per)
+    if dom == "spread":
+        flops = n * 2.0 * P ** 3  # one FMA per support point
+        return dict(kernel="k_spread", bound="alu", achieved=flops / t / 1e12, peak=peak_alu, unit="TFLOP/s",
+                    frac=flops / t / 1e12 / peak_alu, traffic=committed_traffic("k_spread", workload_name),
+                    algorithmic=f"{2 * P ** 3} flop/particle", stage_ms=per)
+    if dom == "fourier":
+        # read + write of the real grid twice (z passes) and of every slab row in the 2-D passes
+        byts = grid_pts * word * 4
+        return dict(kernel="fourier passes", bound="hbm", achieved=byts / t / 1e9, peak=peaks["hbm_gbs"],
+                    unit="GB/s", frac=byts / t / 1e9 / peaks["hbm_gbs"], traffic=None,
+                    algorithmic=f"{byts} B/step", stage_ms=per)
+    if dom == "real":
+        # erfc/exp pair evaluations inside rc: ~ N * rho * 4/3 pi rc^3 pairs, ~40 flops each
+        pairs = n * info["density"] * 4.0 / 3.0 * math.pi * info["rc"] ** 3
+        flops = pairs * 40.0
+        return dict(kernel="k_real", bound="alu", achieved=flops / t / 1e12, peak=peak_alu, unit="TFLOP/s",
+                    frac=flops / t / 1e12 / peak_alu, traffic=committed_traffic("k_real", workload_name),
+                    algorithmic="40 flop/pair inside rc", stage_ms=per)
+    byts = n * 64.0
+    return dict(kernel=dom, bound="hbm", achieved=byts / t / 1e9, peak=peaks["hbm_gbs"], unit="GB/s",
+                frac=byts / t / 1e9 / peaks["hbm_gbs"], traffic=None, algorithmic="64 B/particle", stage_ms=per)
+
+
+def kernels_per_eval(info, real_space):
+    """Kernels one se1p_eval launches: pack, scan, scatter, spread, z forward, three passes
+    per active slab class, z inverse, gather, real space, finalize, energy."""
+    k3 = info["M3"] // 2 + 1
+    classes = 1 + (info["n_I_modes"] > 0) + (k3 - 1 - info["n_I_modes"] > 0)
+    return 4 + 1 + 3 * classes + 1 + 1 + (1 if real_space else 0) + 2
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank, world, local_rank):
+    import torch
+
+    from paper_1611_09538_gb300 import build as lib_build
+    from paper_1611_09538_gb300 import se1p
+
+    lib_build.build()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    sys_ = workload(args.workload)
+    p = sys_.params
+    n = len(sys_.q)
+    prec = se1p.SE1P_MIXED if args.precision == "mixed" else se1p.SE1P_FP64
+    mk = lambda pr: se1p.Plan(sys_.L, p["xi"], p["M"], p["P"], n, Mt=p["Mt"], n0=p["n0"], nI=p["nI"],
+                              nl=p["nl"], rc=p["rc"], precision=pr)
+    plan = mk(prec)
+    info = se1p.se1p_plan_info_copy(se1p.se1p_plan_get_info(plan.handle))
+    info["density"] = n / (sys_.L[0] * sys_.L[1] * sys_.L[2])
+    info["rc"] = p["rc"]
+    x = torch.as_tensor(sys_.x, device="cuda").contiguous()
+    q = torch.as_tensor(sys_.q, device="cuda").contiguous()
+    phi = torch.empty(n, dtype=torch.float64, device="cuda")
+    F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    E = torch.empty(1, dtype=torch.float64, device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        se1p.se1p_eval(plan.handle, n, x, q, phi, F, E, stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    st = se1p.se1p_plan_sync_status(plan.handle, stream)
+    if st != 0:
+        raise RuntimeError(f"device status {se1p.STATUS.get(st)}")
+    if args.profile_only:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile_only": True, "steps": args.steps,
+                              "ms_per_step_wall": 1e3 * (time.perf_counter() - t0) / args.steps}))
+        return
+
+    # accuracy against FP64 on the GPU (untimed)
+    acc = {}
+    if rank == 0:
+        ref = mk(se1p.SE1P_FP64)
+        r64 = ref.eval(x, q)
+        r = plan.eval(x, q)
+        acc = {"phi_rel_rms_vs_fp64_gpu": rel_rms(r.phi.cpu().numpy(), r64.phi.cpu().numpy()),
+               "force_rel_rms_vs_fp64_gpu": rel_rms(r.force.cpu().numpy(), r64.force.cpu().numpy()),
+               "energy_rel_vs_fp64_gpu": abs(r.energy.item() - r64.energy.item()) / abs(r64.energy.item())}
+        phi64 = r64.phi.cpu().numpy()
+        F64 = r64.force.cpu().numpy()
+        phim = r.phi.cpu().numpy()
+        Fm = r.force.cpu().numpy()
+        ref.close()
+
+    sampler = ClockSampler(local_rank)
+    time.sleep(0.25)
+    se1p.se1p_plan_set_profiling(plan.handle, True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    stage_ms, n_evals = se1p.se1p_plan_stage_times(plan.handle)
+    se1p.se1p_plan_set_profiling(plan.handle, False)
+    clocks = sampler.stop()
+    st = se1p.se1p_plan_sync_status(plan.handle, stream)
+    if st != 0:
+        raise RuntimeError(f"device status {se1p.STATUS.get(st)}")
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+
+    # end to end through the host entry point: pinned host buffers, H2D + eval + D2H each step
+    xh = torch.as_tensor(sys_.x).contiguous().pin_memory()
+    qh = torch.as_tensor(sys_.q).contiguous().pin_memory()
+    phih = torch.empty(n, dtype=torch.float64).pin_memory()
+    Fh = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    Eh = torch.empty(1, dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, min(args.steps, 50))
+    for _ in range(2):
+        se1p.se1p_eval_host(plan.handle, n, xh.numpy(), qh.numpy(), phih.numpy(), Fh.numpy(), Eh.numpy(), stream)
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        se1p.se1p_eval_host(plan.handle, n, xh.numpy(), qh.numpy(), phih.numpy(), Fh.numpy(), Eh.numpy(), stream)
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = t.item()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_src = read_peaks()
+    ms_per_step = total_ms / args.steps
+    value = world * n * args.steps / (total_ms * 1e-3)
+    rf = roofline(stage_ms, n_evals, info, n, args.precision, peaks, clocks and clocks["sm_mhz"], args.workload)
+    rf["peak_source"] = ("derived: 152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz" if rf["bound"] == "alu"
+                         else f"{peak_src} hbm_gbs")
+    launches_per_eval = kernels_per_eval(info, p["rc"] > 0)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": dict(workload_config(sys_, args.workload, args.precision),
+                       parallelism="replicas" if world > 1 else "single"),
+        "roofline": {k: rf[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")},
+        "roofline_detail": {"kernel": rf["kernel"], "algorithmic": rf["algorithmic"],
+                            "peak_source": rf["peak_source"], "stage_ms_per_step": rf["stage_ms"]},
+        "e2e": {"value": world * n * e2e_steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(n * 4 * 8), "d2h_bytes_per_step": int(n * 4 * 8 + 8)},
+        "gpu_launches": int(launches_per_eval * args.steps),
+        "clocks": clocks,
+        "accuracy": acc,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        cb = oracle_sample(sys_, args.cpu_seconds)
+        t = cb["targets"]
+        out["cpu_baseline"] = {"value": cb["rate"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                               "sample": f"direct Ewald1P sums (Eqs. 2.2-2.5) for {len(t)} random targets "
+                                         f"against all {n} sources, {cb['seconds']:.1f} s"}
+        acc["phi_rel_rms_fp64_gpu_vs_oracle_sample"] = rel_rms(phi64[t], cb["phi"])
+        acc["force_rel_rms_fp64_gpu_vs_oracle_sample"] = rel_rms(F64[t], cb["F"])
+        acc["phi_rel_rms_mixed_vs_oracle_sample"] = rel_rms(phim[t], cb["phi"])
+        acc["force_rel_rms_mixed_vs_oracle_sample"] = rel_rms(Fm[t], cb["F"])
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+def oracle_step(sys_, n_sources, seed):
+    """One reference step: the direct sums for one target against n_sources of the N sources.
+    The oracle's cost is linear in the sources, so the step stands for n_sources/N of one
+    full target; returns (seconds, full-target equivalents)."""
+    from oracle import direct
+    p = sys_.params
+    n = len(sys_.q)
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(n, size=n_sources, replace=False)
+    xs, qs = sys_.x[idx], sys_.q[idx]
+    t0 = time.perf_counter()
+    direct.ewald1p_parts(xs, qs, sys_.L[2], p["xi"], p["rc"], targets=[0])
+    return time.perf_counter() - t0, n_sources / n
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import direct
+    direct.build()
+    sys_ = workload(args.workload)
+    n = len(sys_.q)
+    # size the per-step sample so that warm-up + steps take about two minutes
+    per_step_budget = max(0.05, min(20.0, 120.0 / max(args.steps + args.warmup, 1)))
+    probe_src = min(n, 2000)
+    t_probe, _ = oracle_step(sys_, probe_src, 99)
+    n_src = int(min(n, max(100, probe_src * per_step_budget / max(t_probe, 1e-6))))
+    for i in range(args.warmup):
+        oracle_step(sys_, n_src, 1000 + i)
+    total_t, total_n = 0.0, 0.0
+    for i in range(args.steps):
+        t, frac = oracle_step(sys_, n_src, 2000 + i)
+        total_t += t
+        total_n += frac
+    cores = direct.num_threads()
+    value = total_n / total_t
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(sys_, args.workload, "fp64 oracle"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: direct Ewald1P sums for 1 target against {n_src} of the {n} "
+                                   f"sources (cost linear in sources; rate in full-target equivalents)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * se1p.h - C ABI of the GB300 (sm_103a) singly periodic Spectral Ewald library.
+ *
+ * The library evaluates the electrostatic potential, force and energy of N
+ * point charges in a box [0,L1) x [0,L2) x [0,L3) that is periodic in z and
+ * free in x and y, by the SE1P method of Saffar Shamshirgar & Tornberg ("The
+ * Spectral Ewald method for singly periodic domains"):
+ *
+ *   phi = phi^R + phi^F + phi^self                                (Eq. 2.1)
+ *   phi^R    : erfc real-space sum over a cell list, r <= rc      (Eq. 2.2)
+ *   phi^F    : Algorithm 1 - Gaussian gridding (Eq. 3.4), adaptive FFT
+ *              (Algorithm 2), scaling with the Ewald Green's function and the
+ *              truncated 2-D kernel at k3 = 0 (Eqs. 3.5-3.10), inverse
+ *              adaptive FFT (Algorithm 3), Gaussian gathering (Eq. 3.11) and
+ *              its analytic gradient for the force (Eq. 3.25)
+ *   phi^self : -2 xi/sqrt(pi) q_m                                 (Eq. 2.5)
+ *   F_m      : -q_m grad phi(x_m); U = 1/2 sum_m q_m phi_m        (Section 3.5)
+ *
+ * Conventions shared by every entry point:
+ *   - Particle arrays are caller-owned and never freed by the library.
+ *     x is [n][3] doubles (x, y, z interleaved), q is [n] doubles, phi is [n],
+ *     force is [n][3], energy is one double.  Results follow the caller's
+ *     particle order.  Entry points named *_host take host pointers; all
+ *     others take device pointers of the current CUDA device.
+ *   - x and y must lie in [0, L1) and [0, L2); z is wrapped into [0, L3).
+ *     sum(q) must vanish: |sum q| <= 1e-12 sum |q| (Section 2.1).
+ *   - Device-side checks (box, finiteness, neutrality) cannot stop an
+ *     asynchronous call: the call runs to completion on sanitised values and
+ *     records the problem in the plan's status word.  se1p_plan_sync_status()
+ *     synchronises the stream and returns (then clears) that word.
+ *   - A plan owns all of its device workspace; it may be used by one stream at
+ *     a time.  Calls are asynchronous on `stream` (a cudaStream_t passed as
+ *     void*; NULL = legacy default stream) unless stated otherwise.
+ *   - Host-side argument errors are returned immediately and launch nothing.
+ */
+#ifndef SE1P_H
+#define SE1P_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SE1P_OK = 0,
+    SE1P_ERR_INVALID_ARG = 1, /* bad pointer, size or parameter                        */
+    SE1P_ERR_NOT_NEUTRAL = 2, /* |sum q| > 1e-12 sum |q|                                 */
+    SE1P_ERR_OUT_OF_BOX = 3,  /* some x or y outside [0, L)                              */
+    SE1P_ERR_ALLOC = 4,       /* device or pinned-host allocation failed                 */
+    SE1P_ERR_CUDA = 5,        /* a CUDA runtime call or kernel launch failed             */
+    SE1P_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                           */
+    SE1P_ERR_NAN = 7,         /* non-finite position or charge                           */
+    SE1P_ERR_CAPACITY = 8     /* n larger than the plan's n_max, or a cell too crowded   */
+} se1p_status;
+
+typedef enum { SE1P_FP64 = 0, SE1P_MIXED = 1 } se1p_precision;
+
+/*
+ * Problem and method parameters (Algorithm 1 INPUT; Section 4.3 recipe).
+ * Fields marked "0 = auto" are chosen by the plan:
+ *   Mt  : smallest 2^a 3^b 5^c 7^d >= M + P (extra points are zero padding)
+ *   n0  : smallest such size >= s0 Mt, s0 defaulting to 2 sqrt(2) >= 1 + sqrt(2)
+ *   nI  : smallest such size >= sl Mt, sl defaulting to the smallest value with
+ *         e^{-2 pi sl} < tol (Eq. 4.8)
+ *   nl  : round(M3 / 10) (Eq. 4.9), at least 1
+ */
+typedef struct {
+    double L[3];   /* box lengths; x, y free, z periodic                                */
+    double xi;     /* Ewald splitting parameter                                         */
+    int M[3];      /* grid points: M[0] = M[1] over [0, L) in x, y; M[2] along z        */
+    int P;         /* Gaussian support in grid points per axis, 2 <= P <= min(M[2], 32) */
+    int Mt;        /* grid points per free axis incl. the extension; 0 = auto          */
+    int n0;        /* padded 2-D FFT size of the k3 = 0 slab; 0 = auto                 */
+    int nI;        /* padded 2-D FFT size of the slabs in the set I; 0 = auto          */
+    int nl;        /* local pad size: I = {0 < |k3| <= 2 pi nl / L1}; < 0 = auto        */
+    double s0;     /* k3 = 0 upsampling used when n0 == 0 (<= 0: 2 sqrt 2)             */
+    double sl;     /* I-set upsampling used when nI == 0 (<= 0: from tol)              */
+    double rc;     /* real-space cutoff; <= 0 skips phi^R (k-space and self only)      */
+    double tol;    /* tolerance for the automatic choices (<= 0: 1e-10)                */
+    int precision; /* se1p_precision                                                    */
+    int flags;     /* reserved, must be 0                                               */
+} se1p_params;
+
+/* Resolved plan geometry (read-only view). */
+typedef struct {
+    int Mt, M3, n0, nI, nl;
+    int n_I_modes;          /* number of k3 > 0 modes in the set I                         */
+    int P, precision;
+    double h, hz;           /* grid spacing in x,y and in z                               */
+    double eta, etaz;       /* Gaussian shape eta = P xi^2 h^2/(c^2 pi), c = 0.95 (Eq. 3.3) */
+    double R;               /* truncation radius of the 2-D kernel, sqrt(2) Mt h          */
+    int cells[3];           /* real-space cell list dimensions                            */
+    size_t workspace_bytes; /* device memory owned by the plan                            */
+} se1p_plan_info;
+
+typedef struct se1p_plan se1p_plan;
+
+/* Create a plan for systems of up to n_max particles on the current device.
+ * Validates params (SE1P_ERR_INVALID_ARG), resolves the automatic fields,
+ * allocates the workspace (SE1P_ERR_ALLOC) and precomputes, in FP64 on the
+ * device, the k3 = 0 scaling table 4 pi e^{-(1-eta) kappa^2/4 xi^2} G_R(kappa)
+ * (Eqs. 3.9-3.10).  Synchronous.  *plan is NULL on failure. */
+se1p_status se1p_plan_create(const se1p_params *params, int n_max, se1p_plan **plan);
+
+/* Free a plan and its workspace (synchronises the device first).  NULL is a no-op. */
+se1p_status se1p_plan_destroy(se1p_plan *plan);
+
+/* Fill *info with the resolved geometry. */
+se1p_status se1p_plan_get_info(const se1p_plan *plan, se1p_plan_info *info);
+
+/* Full evaluation (Algorithm 1 + Eq. 2.2 + Eq. 2.5 + Section 3.5), device pointers.
+ * Any of phi, force, energy may be NULL.  0 <= n <= n_max; n == 0 writes a zero
+ * energy and nothing else.  energy receives U = 1/2 sum q_m phi_m (FP64 reduction). */
+se1p_status se1p_eval(se1p_plan *plan, int n, const double *x, const double *q, double *phi,
+                      double *force, double *energy, void *stream);
+
+/* Same as se1p_eval with host pointers: copies x, q to the plan's device buffers,
+ * evaluates, copies the results back and synchronises `stream`.  Returns the
+ * device status word (as se1p_plan_sync_status) when the launches succeeded. */
+se1p_status se1p_eval_host(se1p_plan *plan, int n, const double *x, const double *q,
+                           double *phi, double *force, double *energy, void *stream);
+
+/* ---- single steps, for verification of one stage at a time (device pointers) ---- */
+
+/* Gridding, Algorithm 1 step 2 (Eq. 3.4): H on the M3 x Mt x Mt grid, written
+ * as grid[(z * Mt + y) * Mt + x] in doubles (converted from FP32 in mixed mode).
+ * The free-axis grid origin is at -P h/2, i.e. particle x sits at x + P h/2. */
+se1p_status se1p_spread(se1p_plan *plan, int n, const double *x, const double *q, double *grid,
+                        void *stream);
+
+/* Algorithm 1 steps 3-5: AFT (Algorithm 2), scaling (Eq. 3.5), AIFT (Algorithm 3),
+ * from grid_in (H) to grid_out (the scaled-and-filtered grid), same layout as
+ * se1p_spread.  grid_in and grid_out may alias. */
+se1p_status se1p_fourier(se1p_plan *plan, const double *grid_in, double *grid_out, void *stream);
+
+/* Algorithm 1 step 6 (Eq. 3.11) and Eq. 3.25: phi^F and F^F at the particles from
+ * a grid in the se1p_spread layout.  Writes (does not accumulate) phi and force;
+ * either may be NULL. */
+se1p_status se1p_gather(se1p_plan *plan, int n, const double *x, const double *q,
+                        const double *grid, double *phi, double *force, void *stream);
+
+/* Real-space part, Eq. 2.2 and its force (Eq. 3.22), over a cell list with cells
+ * no smaller than rc.  Writes (does not accumulate) phi and force.  Requires
+ * params.rc > 0 and rc <= L3. */
+se1p_status se1p_real_space(se1p_plan *plan, int n, const double *x, const double *q, double *phi,
+                            double *force, void *stream);
+
+/* ---- per-stage timing ---- */
+
+/* Stages of se1p_eval timed by the profiling events (one CUDA event pair per
+ * stage, recorded on the evaluation stream). */
+typedef enum {
+    SE1P_STAGE_PACK = 0,    /* validation, counting sort, window tables          */
+    SE1P_STAGE_SPREAD = 1,  /* gridding, Eq. 3.4                                  */
+    SE1P_STAGE_FOURIER = 2, /* AFT + scaling + AIFT (Algorithms 2-3, Eq. 3.5)     */
+    SE1P_STAGE_GATHER = 3,  /* gathering of phi and F, Eqs. 3.11 and 3.25         */
+    SE1P_STAGE_REAL = 4,    /* real-space sum, Eq. 2.2                            */
+    SE1P_STAGE_FINAL = 5,   /* outputs in caller order and the energy reduction   */
+    SE1P_NUM_STAGES = 6
+} se1p_stage;
+
+/* Enable (1) or disable (0) per-stage event recording for subsequent se1p_eval
+ * calls (at most 4096 evaluations are kept).  Enabling clears earlier records.
+ * Synchronous. */
+se1p_status se1p_plan_set_profiling(se1p_plan *plan, int enable);
+
+/* Synchronise the device and return, per stage, the summed elapsed milliseconds
+ * over all recorded evaluations (ms[SE1P_NUM_STAGES]) and their number
+ * (*n_evals); then clear the records. */
+se1p_status se1p_plan_stage_times(se1p_plan *plan, double *ms, int *n_evals);
+
+/* Synchronise `stream` and return the device status word (SE1P_OK or the first
+ * error recorded since the last call), then clear it. */
+se1p_status se1p_plan_sync_status(se1p_plan *plan, void *stream);
+
+/* Static, human-readable name of a status code. */
+const char *se1p_status_string(se1p_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SE1P_H */

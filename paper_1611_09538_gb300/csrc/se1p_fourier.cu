@@ -1,0 +1,297 @@
+// Fourier-side kernels of the SE1P path: the adaptive FFT (Algorithm 2), the
+// scaling step (Eq. 3.5 with the Green's functions of Eqs. 3.6-3.10) and the
+// inverse adaptive FFT (Algorithm 3).
+//
+// Passes (all transforms are hand-written Stockham FFTs in shared memory):
+//   z  : real grid -> k3 = 1..K3-1 complex slabs (and the k3 = 0 slab summed in FP64)
+//   xf : per slab row, zero-pad Mt -> ns and FFT along x            (ns = n0, nI or Mt)
+//   y  : per slab column, zero-pad Mt -> ns, FFT along y, multiply by the
+//        symbol, inverse FFT, keep the Mt spreading rows            (Algorithm 3 step 2-3 crop)
+//   xi : per slab row, inverse FFT along x, keep Mt points
+//   zi : Hermitian completion along z and inverse FFT -> real grid
+// The k3 = 0 slab (Vico-truncated 2-D kernel) always runs in FP64.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "se1p_plan.h"
+
+namespace se1p {
+
+namespace {
+
+__device__ __forceinline__ int signed_index(int i, int n) { return i <= (n - 1) / 2 ? i : i - n; }
+
+// ---- z forward: CTA = (y, chunk of xb x-values); smem [z][p]
+template <typename T>
+__global__ void k_zfwd(int M3, int Mt, int K3, FftDesc d, const Cx<T> *__restrict__ tw, int xb,
+                       const T *__restrict__ grid, Cx<T> *__restrict__ zspec, double *__restrict__ slab0)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
+    Cx<T> *b = a + (size_t)M3 * xb;
+    const int nxc = (Mt + xb - 1) / xb;
+    const int y = blockIdx.x / nxc, x0 = (blockIdx.x % nxc) * xb;
+    for (int e = threadIdx.x; e < M3 * xb; e += blockDim.x) {
+        const int z = e / xb, p = e % xb, x = x0 + p;
+        const T v = x < Mt ? grid[((size_t)z * Mt + y) * Mt + x] : (T)0;
+        a[e] = cx<T>(v, (T)0);
+    }
+    __syncthreads();
+    // k3 = 0 coefficient, summed in FP64 from the stored grid values
+    for (int p = threadIdx.x; p < xb; p += blockDim.x) {
+        const int x = x0 + p;
+        if (x < Mt) {
+            double s = 0.0;
+            for (int z = 0; z < M3; ++z) s += (double)a[z * xb + p].re;
+            slab0[(size_t)y * Mt + x] = s;
+        }
+    }
+    __syncthreads();
+    Cx<T> *res = fft_smem<T>(a, b, d, xb, 1, xb, tw, -1);
+    for (int e = threadIdx.x; e < (K3 - 1) * xb; e += blockDim.x) {
+        const int k = 1 + e / xb, p = e % xb, x = x0 + p;
+        if (x < Mt) zspec[((size_t)k * Mt + y) * Mt + x] = res[k * xb + p];
+    }
+}
+
+// ---- x forward: CTA = rb rows (slab s, y) of one class; smem [row][ns]
+template <typename T, bool FROM_SLAB0>
+__global__ void k_xfwd(int Mt, int ns, int kfirst, int nrows, FftDesc d, const Cx<T> *__restrict__ tw, int rb,
+                       const Cx<T> *__restrict__ zspec, const double *__restrict__ slab0, Cx<T> *__restrict__ rows)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
+    Cx<T> *b = a + (size_t)rb * ns;
+    const int r0 = blockIdx.x * rb;
+    for (int e = threadIdx.x; e < rb * ns; e += blockDim.x) {
+        const int p = e / ns, j = e % ns, r = r0 + p;
+        Cx<T> v = cx<T>((T)0, (T)0);
+        if (r < nrows && j < Mt) {
+            const int s = r / Mt, y = r % Mt;
+            if (FROM_SLAB0) v = cx<T>((T)slab0[(size_t)y * Mt + j], (T)0);
+            else v = zspec[((size_t)(kfirst + s) * Mt + y) * Mt + j];
+        }
+        a[e] = v;
+    }
+    __syncthreads();
+    Cx<T> *res = fft_smem<T>(a, b, d, rb, ns, 1, tw, -1);
+    for (int e = threadIdx.x; e < rb * ns; e += blockDim.x) {
+        const int p = e / ns, r = r0 + p;
+        if (r < nrows) rows[(size_t)r * ns + (e % ns)] = res[e];
+    }
+}
+
+// ---- y pass with the scaling: CTA = (slab, chunk of xb columns); smem [y][p]
+// Class 0 (k3 = 0) reads the FP64 symbol table; other classes build
+//   4 pi / (ns^2 M3) * ex[kx] ex[ky] ez[k3] / (kappa^2 + k3^2).
+template <typename T, bool CLASS0>
+__global__ void k_yscale(int Mt, int ns, int kfirst, int count, FftDesc d, const Cx<T> *__restrict__ tw, int xb,
+                         Cx<T> *__restrict__ rows, const double *__restrict__ sym0, const T *__restrict__ ex,
+                         const T *__restrict__ ez, double dkap, double dk3, double norm)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
+    Cx<T> *b = a + (size_t)ns * xb;
+    const int nkc = (ns + xb - 1) / xb;
+    const int s = blockIdx.x / nkc, kx0 = (blockIdx.x % nkc) * xb;
+    Cx<T> *slab = rows + (size_t)s * Mt * ns;
+    for (int e = threadIdx.x; e < ns * xb; e += blockDim.x) {
+        const int y = e / xb, p = e % xb, kx = kx0 + p;
+        a[e] = (y < Mt && kx < ns) ? slab[(size_t)y * ns + kx] : cx<T>((T)0, (T)0);
+    }
+    __syncthreads();
+    Cx<T> *res = fft_smem<T>(a, b, d, xb, 1, xb, tw, -1);
+    Cx<T> *oth = res == a ? b : a;
+    const int k3i = kfirst + s;
+    for (int e = threadIdx.x; e < ns * xb; e += blockDim.x) {
+        const int ky = e / xb, p = e % xb, kx = kx0 + p;
+        T S = (T)0;
+        if (kx < ns) {
+            if (CLASS0) {
+                S = (T)sym0[(size_t)ky * ns + kx];
+            } else {
+                const T kxv = (T)(dkap * signed_index(kx, ns)), kyv = (T)(dkap * signed_index(ky, ns));
+                const T k3v = (T)(dk3 * k3i);
+                S = (T)norm * ex[kx] * ex[ky] * ez[k3i] / (kxv * kxv + kyv * kyv + k3v * k3v);
+            }
+        }
+        res[e] = scale(res[e], S);
+    }
+    __syncthreads();
+    res = fft_smem<T>(res, oth, d, xb, 1, xb, tw, +1);
+    for (int e = threadIdx.x; e < Mt * xb; e += blockDim.x) {
+        const int y = e / xb, p = e % xb, kx = kx0 + p;
+        if (kx < ns) slab[(size_t)y * ns + kx] = res[e];
+    }
+}
+
+// ---- x inverse: CTA = rb rows; inverse FFT along x, keep the first Mt points
+template <typename T, bool TO_SLAB0>
+__global__ void k_xinv(int Mt, int ns, int kfirst, int nrows, FftDesc d, const Cx<T> *__restrict__ tw, int rb,
+                       const Cx<T> *__restrict__ rows, Cx<T> *__restrict__ zspec, double *__restrict__ slab0)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
+    Cx<T> *b = a + (size_t)rb * ns;
+    const int r0 = blockIdx.x * rb;
+    for (int e = threadIdx.x; e < rb * ns; e += blockDim.x) {
+        const int p = e / ns, r = r0 + p;
+        a[e] = r < nrows ? rows[(size_t)r * ns + (e % ns)] : cx<T>((T)0, (T)0);
+    }
+    __syncthreads();
+    Cx<T> *res = fft_smem<T>(a, b, d, rb, ns, 1, tw, +1);
+    for (int e = threadIdx.x; e < rb * Mt; e += blockDim.x) {
+        const int p = e / Mt, x = e % Mt, r = r0 + p;
+        if (r >= nrows) continue;
+        const int s = r / Mt, y = r % Mt;
+        const Cx<T> v = res[p * ns + x];
+        if (TO_SLAB0) slab0[(size_t)y * Mt + x] = (double)v.re;
+        else zspec[((size_t)(kfirst + s) * Mt + y) * Mt + x] = v;
+    }
+}
+
+// ---- z inverse: Hermitian completion along z, inverse FFT, real part
+template <typename T>
+__global__ void k_zinv(int M3, int Mt, int K3, FftDesc d, const Cx<T> *__restrict__ tw, int xb,
+                       const Cx<T> *__restrict__ zspec, const double *__restrict__ slab0, T *__restrict__ grid)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
+    Cx<T> *b = a + (size_t)M3 * xb;
+    const int nxc = (Mt + xb - 1) / xb;
+    const int y = blockIdx.x / nxc, x0 = (blockIdx.x % nxc) * xb;
+    for (int e = threadIdx.x; e < M3 * xb; e += blockDim.x) {
+        const int k = e / xb, p = e % xb, x = x0 + p;
+        Cx<T> v = cx<T>((T)0, (T)0);
+        if (x < Mt) {
+            if (k == 0) {
+                v = cx<T>((T)slab0[(size_t)y * Mt + x], (T)0);
+            } else if (k < K3) {
+                v = zspec[((size_t)k * Mt + y) * Mt + x];
+            } else {
+                const Cx<T> c = zspec[((size_t)(M3 - k) * Mt + y) * Mt + x];
+                v = cx<T>(c.re, -c.im);
+            }
+        }
+        a[e] = v;
+    }
+    __syncthreads();
+    Cx<T> *res = fft_smem<T>(a, b, d, xb, 1, xb, tw, +1);
+    for (int e = threadIdx.x; e < M3 * xb; e += blockDim.x) {
+        const int z = e / xb, p = e % xb, x = x0 + p;
+        if (x < Mt) grid[((size_t)z * Mt + y) * Mt + x] = res[e].re;
+    }
+}
+
+// ---- k3 = 0 scaling table in FP64 (Eqs. 3.5, 3.9-3.10), including 1/(n0^2 M3)
+__global__ void k_vico(int n0, double dkap, double R, double xi, double eta, double norm, double *__restrict__ sym)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n0 * n0) return;
+    const int kx = i % n0, ky = i / n0;
+    const double ax = dkap * signed_index(kx, n0), ay = dkap * signed_index(ky, n0);
+    const double k2 = ax * ax + ay * ay;
+    double G;
+    if (k2 == 0.0) {
+        G = R * R / 4.0 * (1.0 - 2.0 * log(R));
+    } else {
+        const double k = sqrt(k2);
+        G = (1.0 - j0(R * k)) / k2 - R * log(R) * j1(R * k) / k;
+    }
+    sym[i] = norm * 4.0 * kPi * exp(-(1.0 - eta) * k2 / (4.0 * xi * xi)) * G;
+}
+
+template <typename T> size_t cbytes() { return sizeof(Cx<T>); }
+
+}  // namespace
+
+void launch_vico_table(se1p_plan *p, cudaStream_t s)
+{
+    const int n0 = p->n0;
+    const double dkap = 2.0 * kPi / (n0 * p->geo.h);
+    const double R = sqrt(2.0) * p->Mt * p->geo.h;
+    const double norm = 1.0 / ((double)n0 * n0 * p->M3);
+    k_vico<<<(n0 * n0 + 255) / 256, 256, 0, s>>>(n0, dkap, R, p->geo.xi, p->geo.eta, norm, p->b.sym0);
+}
+
+template <typename T> int configure_fourier_kernels(se1p_plan *p)
+{
+    int dev;
+    cudaGetDevice(&dev);
+    int maxsm = 0;
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaError_t e = cudaSuccess;
+    e = (cudaError_t)(e | cudaFuncSetAttribute(k_zfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    e = (cudaError_t)(e | cudaFuncSetAttribute(k_zinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    e = (cudaError_t)(e | cudaFuncSetAttribute(k_xfwd<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    e = (cudaError_t)(e | cudaFuncSetAttribute(k_xinv<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    e = (cudaError_t)(e | cudaFuncSetAttribute(k_yscale<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    e = (cudaError_t)(e | cudaFuncSetAttribute(k_xfwd<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    e = (cudaError_t)(e | cudaFuncSetAttribute(k_xinv<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    e = (cudaError_t)(e | cudaFuncSetAttribute(k_yscale<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    return e == cudaSuccess ? 0 : -1;
+}
+
+template <typename T> void launch_fourier(se1p_plan *p, cudaStream_t s)
+{
+    const int Mt = p->Mt, M3 = p->M3, K3 = p->K3;
+    const Geo &g = p->geo;
+    // z forward
+    {
+        const int xb = p->xb_z;
+        const int nxc = (Mt + xb - 1) / xb;
+        const size_t sm = 2 * (size_t)M3 * xb * cbytes<T>();
+        k_zfwd<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Cx<T> *)p->b.tw_z, xb, (const T *)p->b.grid,
+                                            (Cx<T> *)p->b.zspec, p->b.slab0_in);
+    }
+    const double norm_base = 4.0 * kPi / M3;
+    for (int c = 0; c < 3; ++c) {
+        const SlabClass &C = p->cls[c];
+        if (C.count == 0) continue;
+        const int nrows = C.count * Mt;
+        const double dkap = 2.0 * kPi / (C.ns * g.h);
+        const double dk3 = 2.0 * kPi / g.L[2];
+        const double norm = norm_base / ((double)C.ns * C.ns);
+        if (c == 0) {
+            const size_t smx = 2 * (size_t)C.rb * C.ns * cbytes<double>();
+            k_xfwd<double, true><<<(nrows + C.rb - 1) / C.rb, 256, smx, s>>>(
+                Mt, C.ns, 0, nrows, C.fd, (const Cx<double> *)C.tw, C.rb, nullptr, p->b.slab0_in, (Cx<double> *)C.rows);
+            const int nkc = (C.ns + C.xb - 1) / C.xb;
+            const size_t smy = 2 * (size_t)C.ns * C.xb * cbytes<double>();
+            k_yscale<double, true><<<C.count * nkc, 256, smy, s>>>(Mt, C.ns, 0, C.count, C.fd, (const Cx<double> *)C.tw,
+                                                                  C.xb, (Cx<double> *)C.rows, p->b.sym0, nullptr,
+                                                                  nullptr, dkap, dk3, norm);
+            k_xinv<double, true><<<(nrows + C.rb - 1) / C.rb, 256, smx, s>>>(
+                Mt, C.ns, 0, nrows, C.fd, (const Cx<double> *)C.tw, C.rb, (const Cx<double> *)C.rows, nullptr,
+                p->b.slab0_out);
+        } else {
+            const size_t smx = 2 * (size_t)C.rb * C.ns * cbytes<T>();
+            k_xfwd<T, false><<<(nrows + C.rb - 1) / C.rb, 256, smx, s>>>(
+                Mt, C.ns, C.kfirst, nrows, C.fd, (const Cx<T> *)C.tw, C.rb, (const Cx<T> *)p->b.zspec, nullptr,
+                (Cx<T> *)C.rows);
+            const int nkc = (C.ns + C.xb - 1) / C.xb;
+            const size_t smy = 2 * (size_t)C.ns * C.xb * cbytes<T>();
+            k_yscale<T, false><<<C.count * nkc, 256, smy, s>>>(Mt, C.ns, C.kfirst, C.count, C.fd, (const Cx<T> *)C.tw,
+                                                              C.xb, (Cx<T> *)C.rows, nullptr, (const T *)C.ex,
+                                                              (const T *)p->b.ez, dkap, dk3, norm);
+            k_xinv<T, false><<<(nrows + C.rb - 1) / C.rb, 256, smx, s>>>(
+                Mt, C.ns, C.kfirst, nrows, C.fd, (const Cx<T> *)C.tw, C.rb, (const Cx<T> *)C.rows, (Cx<T> *)p->b.zspec,
+                nullptr);
+        }
+    }
+    // z inverse
+    {
+        const int xb = p->xb_z;
+        const int nxc = (Mt + xb - 1) / xb;
+        const size_t sm = 2 * (size_t)M3 * xb * cbytes<T>();
+        k_zinv<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Cx<T> *)p->b.tw_z, xb,
+                                            (const Cx<T> *)p->b.zspec, p->b.slab0_out, (T *)p->b.grid);
+    }
+}
+
+template void launch_fourier<float>(se1p_plan *, cudaStream_t);
+template void launch_fourier<double>(se1p_plan *, cudaStream_t);
+template int configure_fourier_kernels<float>(se1p_plan *);
+template int configure_fourier_kernels<double>(se1p_plan *);
+
+}  // namespace se1p

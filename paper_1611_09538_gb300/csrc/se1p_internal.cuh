@@ -1,0 +1,249 @@
+// Internal declarations shared by the translation units of libse1p.
+//
+// Grid layout (all precisions): real grids are [z][y][x] with x fastest,
+// M3 x Mt x Mt points; the free-axis origin is at -P h/2 (a particle at x sits
+// at x + P h/2 on [0, Mt h)), z is periodic with M3 points.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "se1p.h"
+
+namespace se1p {
+
+// ------------------------------------------------------------------ status bits
+enum : int {
+    FLAG_OUT_OF_BOX = 1,
+    FLAG_NAN = 2,
+    FLAG_NOT_NEUTRAL = 4,
+    FLAG_CAPACITY = 8,
+    FLAG_TIMEOUT = 16,
+};
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+// ------------------------------------------------------------------ complex
+template <typename T> struct Cx;
+template <> struct __align__(8) Cx<float> { float re, im; };
+template <> struct __align__(16) Cx<double> { double re, im; };
+
+template <typename T> __device__ __forceinline__ Cx<T> cx(T re, T im) { Cx<T> r; r.re = re; r.im = im; return r; }
+template <typename T> __device__ __forceinline__ Cx<T> operator+(Cx<T> a, Cx<T> b) { return cx<T>(a.re + b.re, a.im + b.im); }
+template <typename T> __device__ __forceinline__ Cx<T> operator-(Cx<T> a, Cx<T> b) { return cx<T>(a.re - b.re, a.im - b.im); }
+template <typename T> __device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b)
+{
+    return cx<T>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+// multiply by s*i, s = +-1
+template <typename T> __device__ __forceinline__ Cx<T> mul_si(Cx<T> a, int s)
+{
+    return s > 0 ? cx<T>(-a.im, a.re) : cx<T>(a.im, -a.re);
+}
+template <typename T> __device__ __forceinline__ Cx<T> scale(Cx<T> a, T s) { return cx<T>(a.re * s, a.im * s); }
+
+// ------------------------------------------------------------------ FFT descriptor
+// A length-n transform factored into radices (applied first to last).  The
+// twiddle table holds w^t = exp(-2 pi i t / n), t = 0..n-1.
+struct FftDesc {
+    int n;
+    int nrad;
+    int rad[24];
+};
+
+// Small DFTs, X_k = sum_j a_j exp(s 2 pi i j k / R), s = -1 forward, +1 inverse.
+template <typename T> __device__ __forceinline__ void dft2(Cx<T> *v)
+{
+    Cx<T> a = v[0], b = v[1];
+    v[0] = a + b;
+    v[1] = a - b;
+}
+
+template <typename T> __device__ __forceinline__ void dft4(Cx<T> *v, int s)
+{
+    Cx<T> t0 = v[0] + v[2], t1 = v[0] - v[2], t2 = v[1] + v[3], t3 = v[1] - v[3];
+    v[0] = t0 + t2;
+    v[2] = t0 - t2;
+    Cx<T> r = mul_si(t3, s);
+    v[1] = t1 + r;
+    v[3] = t1 - r;
+}
+
+template <typename T> __device__ __forceinline__ void dft8(Cx<T> *v, int s)
+{
+    Cx<T> e[4] = {v[0], v[2], v[4], v[6]};
+    Cx<T> o[4] = {v[1], v[3], v[5], v[7]};
+    dft4(e, s);
+    dft4(o, s);
+    const T r = (T)0.70710678118654752440;
+    // w8^k = exp(s 2 pi i k / 8)
+    Cx<T> w1 = cx<T>(r, s * r), w3 = cx<T>(-r, s * r);
+    Cx<T> o1 = cmul(o[1], w1), o2 = mul_si(o[2], s), o3 = cmul(o[3], w3);
+    v[0] = e[0] + o[0];
+    v[4] = e[0] - o[0];
+    v[1] = e[1] + o1;
+    v[5] = e[1] - o1;
+    v[2] = e[2] + o2;
+    v[6] = e[2] - o2;
+    v[3] = e[3] + o3;
+    v[7] = e[3] - o3;
+}
+
+// Odd radix by symmetric pairs: X_k = a0 + sum_{j=1}^{(R-1)/2} [(a_j + a_{R-j}) c_{jk}
+//                                      + s i (a_j - a_{R-j}) s_{jk}],  c_m = cos(2 pi m/R).
+template <typename T, int R> __device__ __forceinline__ void dft_odd(Cx<T> *v, int s)
+{
+    constexpr int H = (R - 1) / 2;
+    T c[R], sn[R];
+    if constexpr (R == 3) {
+        const T cc[3] = {1, -0.5, -0.5};
+        const T ss[3] = {0, 0.86602540378443864676, -0.86602540378443864676};
+        for (int m = 0; m < R; ++m) { c[m] = cc[m]; sn[m] = ss[m]; }
+    } else if constexpr (R == 5) {
+        const T cc[5] = {1, 0.30901699437494742410, -0.80901699437494742410, -0.80901699437494742410,
+                         0.30901699437494742410};
+        const T ss[5] = {0, 0.95105651629515357212, 0.58778525229247312917, -0.58778525229247312917,
+                         -0.95105651629515357212};
+        for (int m = 0; m < R; ++m) { c[m] = cc[m]; sn[m] = ss[m]; }
+    } else {
+        const T cc[7] = {1, 0.62348980185873353053, -0.22252093395631440429, -0.90096886790241912624,
+                         -0.90096886790241912624, -0.22252093395631440429, 0.62348980185873353053};
+        const T ss[7] = {0, 0.78183148246802980871, 0.97492791218182360702, 0.43388373911755812048,
+                         -0.43388373911755812048, -0.97492791218182360702, -0.78183148246802980871};
+        for (int m = 0; m < R; ++m) { c[m] = cc[m]; sn[m] = ss[m]; }
+    }
+    Cx<T> sp[H], sm[H];
+    Cx<T> x0 = v[0];
+    Cx<T> tot = x0;
+#pragma unroll
+    for (int j = 1; j <= H; ++j) {
+        sp[j - 1] = v[j] + v[R - j];
+        sm[j - 1] = v[j] - v[R - j];
+        tot = tot + sp[j - 1];
+    }
+    v[0] = tot;
+#pragma unroll
+    for (int k = 1; k < R; ++k) {
+        Cx<T> acc = x0;
+        Cx<T> accs = cx<T>(0, 0);
+#pragma unroll
+        for (int j = 1; j <= H; ++j) {
+            int m = (j * k) % R;
+            acc = acc + scale(sp[j - 1], c[m]);
+            accs = accs + scale(sm[j - 1], sn[m]);
+        }
+        v[k] = acc + mul_si(accs, s);
+    }
+}
+
+// One Stockham pass of radix R over `npen` pencils of length n held in shared
+// memory: element j of pencil p lives at buf[p * sp + j * sj].
+template <typename T, int R>
+__device__ __forceinline__ void stockham_pass(const Cx<T> *__restrict__ src, Cx<T> *__restrict__ dst, int n,
+                                              int Ns, int npen, int sp, int sj,
+                                              const Cx<T> *__restrict__ tw, int s)
+{
+    const int nb = n / R;
+    const int total = nb * npen;
+    const int twmul = n / (Ns * R);
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int i, p;
+        if (sj == 1) {
+            i = idx % nb;
+            p = idx / nb;
+        } else {
+            p = idx % npen;
+            i = idx / npen;
+        }
+        const int k = i % Ns;
+        Cx<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[p * sp + (i + r * nb) * sj];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                Cx<T> w = tw[r * k * twmul];
+                if (s > 0) w.im = -w.im;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        if constexpr (R == 2) dft2(v);
+        else if constexpr (R == 4) dft4(v, s);
+        else if constexpr (R == 8) dft8(v, s);
+        else dft_odd<T, R>(v, s);
+        const int base = (i / Ns) * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[p * sp + (base + r * Ns) * sj] = v[r];
+    }
+}
+
+// Batched in-shared-memory FFT (unnormalised; s = -1 forward, +1 inverse).
+// a holds the input, b is scratch of the same shape; returns the buffer that
+// holds the result.  Must be called by all threads of the block.
+template <typename T>
+__device__ Cx<T> *fft_smem(Cx<T> *a, Cx<T> *b, const FftDesc &d, int npen, int sp, int sj,
+                           const Cx<T> *__restrict__ tw, int s)
+{
+    int Ns = 1;
+    for (int st = 0; st < d.nrad; ++st) {
+        const int R = d.rad[st];
+        switch (R) {
+        case 2: stockham_pass<T, 2>(a, b, d.n, Ns, npen, sp, sj, tw, s); break;
+        case 3: stockham_pass<T, 3>(a, b, d.n, Ns, npen, sp, sj, tw, s); break;
+        case 4: stockham_pass<T, 4>(a, b, d.n, Ns, npen, sp, sj, tw, s); break;
+        case 5: stockham_pass<T, 5>(a, b, d.n, Ns, npen, sp, sj, tw, s); break;
+        case 7: stockham_pass<T, 7>(a, b, d.n, Ns, npen, sp, sj, tw, s); break;
+        default: stockham_pass<T, 8>(a, b, d.n, Ns, npen, sp, sj, tw, s); break;
+        }
+        __syncthreads();
+        Cx<T> *t = a;
+        a = b;
+        b = t;
+        Ns *= R;
+    }
+    return a;
+}
+
+// ------------------------------------------------------------------ particles
+
+// Particle record in spread-bin order.  t_a = (coordinate from grid origin)/h_a;
+// i0 is the first support index (free axes in [0, Mt-P], z wrapped into [0, M3));
+// g = t - i0 - c with c = P/2 (even P) or (P-1)/2 (odd P), so grid point
+// i0 + j lies at distance (g - (j - c)) h from the particle.
+template <typename T> struct PartRec {
+    int i0[3];
+    int orig;
+    T g[3];
+    T q;
+};
+
+// Real-space record in cell order: coordinates relative to the cell's lower
+// corner, computed in FP64 and stored as an unevaluated sum hi + lo of two T
+// values (lo = 0 for T = double), charge and caller index.  With FP32 the
+// split keeps close-pair displacements accurate to a few ulps of |d| instead
+// of a few ulps of the cell size.
+template <typename T> struct CellRec {
+    T lx, ly, lz, q;
+    T ex, ey, ez;
+    int orig;
+};
+
+// Geometry passed by value to kernels.
+struct Geo {
+    int M3, Mt, P, K3;
+    int c;            // support centre offset (P/2 or (P-1)/2)
+    int nbx, nby, nbz, nbins;  // spread bins over support-start indices
+    int ncx, ncy, ncz, ncells; // real-space cells
+    double L[3];
+    double h, hz, off;         // spacings, free-axis grid origin shift P h / 2
+    double xi, eta, etaz;
+    double wnorm_xy, wnorm_z;  // (2 xi^2 / (pi eta))^{1/2} per axis
+    double alpha_xy, alpha_z;  // 2 xi^2 h^2 / eta per axis (exponent scale in grid units)
+    double cs[3];              // cell sizes
+    double rc, rc2;
+    int nIm;                   // number of k3 > 0 modes in the set I
+};
+
+constexpr int kBin = 8;  // spread bin / tile edge in grid points
+
+}  // namespace se1p

@@ -1,0 +1,490 @@
+// Particle-side kernels of the SE1P path:
+//   pack + validate -> counting sort into spread bins and real-space cells,
+//   per-particle Gaussian window tables, gridding (Eq. 3.4), gathering
+//   (Eq. 3.11) with its analytic gradient (Eq. 3.25), and the final FP64
+//   energy reduction U = 1/2 sum q phi.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "se1p_plan.h"
+
+namespace se1p {
+
+namespace {
+
+__device__ __forceinline__ int support_start(double t, int P)
+{
+    // even P: floor(t) - P/2 + 1 ... floor(t) + P/2; odd P: centred on round(t)
+    return (P & 1) ? (int)floor(t + 0.5) - (P - 1) / 2 : (int)floor(t) - P / 2 + 1;
+}
+
+__device__ __forceinline__ int imod(int a, int m)
+{
+    int r = a % m;
+    return r < 0 ? r + m : r;
+}
+
+template <typename T> __device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Free-axis and z support starts of a sanitised particle.
+struct Support {
+    int i0[3];
+    double t[3];
+};
+
+__device__ __forceinline__ Support particle_support(const Geo &g, double px, double py, double pz)
+{
+    Support s;
+    const double xs = px + g.off, ys = py + g.off;
+    s.t[0] = xs / g.h;
+    s.t[1] = ys / g.h;
+    s.t[2] = pz / g.hz;
+    const int hi = g.Mt - g.P;
+    s.i0[0] = min(max(support_start(s.t[0], g.P), 0), hi);
+    s.i0[1] = min(max(support_start(s.t[1], g.P), 0), hi);
+    s.i0[2] = support_start(s.t[2], g.P);  // unwrapped
+    return s;
+}
+
+// ------------------------------------------------------------------ pack
+template <typename T>
+__global__ void k_pack(Geo g, int n, const double *__restrict__ x, const double *__restrict__ q,
+                       double *__restrict__ xyzq, int *__restrict__ bin_key, int *__restrict__ cell_key,
+                       int *__restrict__ bin_count, int *__restrict__ cell_count, double *__restrict__ sums,
+                       int *__restrict__ status)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double sq = 0.0, saq = 0.0;
+    if (i < n) {
+        double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2], qq = q[i];
+        int flag = 0;
+        if (!isfinite(px) || !isfinite(py) || !isfinite(pz) || !isfinite(qq)) {
+            flag |= FLAG_NAN;
+            if (!isfinite(px)) px = 0.0;
+            if (!isfinite(py)) py = 0.0;
+            if (!isfinite(pz)) pz = 0.0;
+            qq = 0.0;
+        }
+        if (px < 0.0 || px >= g.L[0] || py < 0.0 || py >= g.L[1]) {
+            flag |= FLAG_OUT_OF_BOX;
+            px = fmin(fmax(px, 0.0), g.L[0] * (1.0 - 1e-15));
+            py = fmin(fmax(py, 0.0), g.L[1] * (1.0 - 1e-15));
+        }
+        if (pz < 0.0 || pz >= g.L[2]) {
+            pz = pz - floor(pz / g.L[2]) * g.L[2];
+            if (pz >= g.L[2] || pz < 0.0) pz = 0.0;
+        }
+        const Support s = particle_support(g, px, py, pz);
+        const int bx = s.i0[0] / kBin, by = s.i0[1] / kBin, bz = imod(s.i0[2], g.M3) / kBin;
+        const int bin = (bz * g.nby + by) * g.nbx + bx;
+        const int cx = min((int)(px / g.cs[0]), g.ncx - 1);
+        const int cy = min((int)(py / g.cs[1]), g.ncy - 1);
+        const int cz = min((int)(pz / g.cs[2]), g.ncz - 1);
+        const int cell = (cz * g.ncy + cy) * g.ncx + cx;
+        reinterpret_cast<double4 *>(xyzq)[i] = make_double4(px, py, pz, qq);
+        bin_key[i] = bin;
+        cell_key[i] = cell;
+        atomicAdd(bin_count + bin, 1);
+        atomicAdd(cell_count + cell, 1);
+        if (flag) atomicOr(status, flag);
+        sq = qq;
+        saq = fabs(qq);
+    }
+    sq = warp_sum(sq);
+    saq = warp_sum(saq);
+    if ((threadIdx.x & 31) == 0 && (sq != 0.0 || saq != 0.0)) {
+        atomicAdd(sums, sq);
+        atomicAdd(sums + 1, saq);
+    }
+}
+
+// Exclusive scans of the bin and cell histograms (one block per array); the
+// first block also checks neutrality, |sum q| <= 1e-12 sum |q| (Section 2.1).
+__global__ void k_scan(int nbins, int ncells, const int *__restrict__ counts, int *__restrict__ starts,
+                       int *__restrict__ cursors, const double *__restrict__ sums, int *__restrict__ status)
+{
+    const int which = blockIdx.x;
+    const int len = which == 0 ? nbins : ncells;
+    const int *c = counts + (which == 0 ? 0 : nbins);
+    int *st = starts + (which == 0 ? 0 : nbins + 1);
+    int *cu = cursors + (which == 0 ? 0 : nbins);
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int base = 0; base < len; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const int v = i < len ? c[i] : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) warp_tot[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            int w = lane < nw ? warp_tot[lane] : 0;
+            int wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += t;
+            }
+            if (lane < nw) warp_tot[lane] = wi - w;  // exclusive warp offsets
+        }
+        __syncthreads();
+        const int excl = carry + warp_tot[wid] + incl - v;
+        if (i < len) {
+            st[i] = excl;
+            cu[i] = excl;
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) st[len] = carry;
+    if (which == 0 && threadIdx.x == 0) {
+        if (fabs(sums[0]) > 1e-12 * sums[1]) atomicOr(status, FLAG_NOT_NEUTRAL);
+    }
+}
+
+// Scatter into bin order (with the window tables) and into cell order.
+template <typename T>
+__global__ void k_scatter(Geo g, int n, const double *__restrict__ xyzq, const int *__restrict__ bin_key,
+                          const int *__restrict__ cell_key, int *__restrict__ bin_cursor,
+                          int *__restrict__ cell_cursor, PartRec<T> *__restrict__ parts, T *__restrict__ wts,
+                          CellRec<T> *__restrict__ cells)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double4 p = reinterpret_cast<const double4 *>(xyzq)[i];
+    const Support s = particle_support(g, p.x, p.y, p.z);
+    const int pos = atomicAdd(bin_cursor + bin_key[i], 1);
+    PartRec<T> r;
+    r.i0[0] = s.i0[0];
+    r.i0[1] = s.i0[1];
+    r.i0[2] = imod(s.i0[2], g.M3);
+    r.orig = i;
+    r.q = (T)p.w;
+    T *w = wts + (size_t)pos * 3 * g.P;
+    for (int a = 0; a < 3; ++a) {
+        const double gg = s.t[a] - s.i0[a] - g.c;  // particle offset from the support centre, grid units
+        r.g[a] = (T)gg;
+        const double alpha = a < 2 ? g.alpha_xy : g.alpha_z;
+        const double wn = a < 2 ? g.wnorm_xy : g.wnorm_z;
+        for (int j = 0; j < g.P; ++j) {
+            const double d = gg - (double)(j - g.c);
+            if (sizeof(T) == sizeof(double)) {
+                w[a * g.P + j] = (T)(wn * exp(-alpha * d * d));
+            } else {
+                w[a * g.P + j] = (T)wn * expf((float)(-alpha * d * d));
+            }
+        }
+    }
+    parts[pos] = r;
+    // cell order, coordinates relative to the cell corner (FP64 difference, stored in T)
+    const int cell = cell_key[i];
+    const int cx = cell % g.ncx, cy = (cell / g.ncx) % g.ncy, cz = cell / (g.ncx * g.ncy);
+    const int cpos = atomicAdd(cell_cursor + cell, 1);
+    CellRec<T> c;
+    const double lx = p.x - cx * g.cs[0], ly = p.y - cy * g.cs[1], lz = p.z - cz * g.cs[2];
+    c.lx = (T)lx;
+    c.ly = (T)ly;
+    c.lz = (T)lz;
+    c.ex = (T)(lx - (double)c.lx);
+    c.ey = (T)(ly - (double)c.ly);
+    c.ez = (T)(lz - (double)c.lz);
+    c.q = (T)p.w;
+    c.orig = i;
+    cells[cpos] = c;
+}
+
+// ------------------------------------------------------------------ gridding (Eq. 3.4)
+//
+// Output-stationary: one CTA owns an 8x8x8 tile of the grid and accumulates
+// every particle whose support overlaps it in registers (no atomics); thread
+// (tz, ty) owns the 8 x-points of one row.  Particles are visited bin by bin
+// (bins of 8 support-start indices per axis), staged 32 at a time as their
+// window values at the tile's 8 offsets per axis (zero outside the support).
+constexpr int kSpreadBatch = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(64) k_spread(Geo g, const int *__restrict__ bin_start,
+                                               const PartRec<T> *__restrict__ parts,
+                                               const T *__restrict__ wts, T *__restrict__ grid)
+{
+    __shared__ T sw[kSpreadBatch][3][kBin];
+    const int ntx = (g.Mt + kBin - 1) / kBin, nty = ntx;
+    const int tile = blockIdx.x;
+    const int txi = tile % ntx, tyi = (tile / ntx) % nty, tzi = tile / (ntx * nty);
+    const int x0 = txi * kBin, y0 = tyi * kBin, z0 = tzi * kBin;
+    const int tz = threadIdx.x >> 3, ty = threadIdx.x & 7;
+    const int P = g.P;
+    T acc[kBin];
+#pragma unroll
+    for (int c = 0; c < kBin; ++c) acc[c] = (T)0;
+
+    // bins whose start indices can reach the tile
+    const int bx_lo = max(x0 - P + 1, 0) / kBin, bx_hi = min(x0 + kBin - 1, g.Mt - P) / kBin;
+    const int by_lo = max(y0 - P + 1, 0) / kBin, by_hi = min(y0 + kBin - 1, g.Mt - P) / kBin;
+    const int span = P + kBin - 1;  // cyclic range of z starts [z0-P+1, z0+7]
+    const bool allz = span + 2 * kBin > g.M3;
+    int u = 0;
+    int zb_iter = 0;
+    while (true) {
+        int bz;
+        if (allz) {
+            if (zb_iter >= g.nbz) break;
+            bz = zb_iter++;
+        } else {
+            if (u >= span) break;
+            const int s = imod(z0 - P + 1 + u, g.M3);
+            bz = s / kBin;
+            u += min((bz + 1) * kBin, g.M3) - s;
+        }
+        if (bx_lo > bx_hi || by_lo > by_hi) continue;
+        for (int by = by_lo; by <= by_hi; ++by) {
+            const int row = (bz * g.nby + by) * g.nbx;
+            const int beg = bin_start[row + bx_lo], end = bin_start[row + bx_hi + 1];
+            for (int b0 = beg; b0 < end; b0 += kSpreadBatch) {
+                const int nb = min(kSpreadBatch, end - b0);
+                for (int e = threadIdx.x; e < nb * 3 * kBin; e += blockDim.x) {
+                    const int b = e / (3 * kBin), r = e % (3 * kBin), a = r / kBin, o = r % kBin;
+                    const PartRec<T> &pr = parts[b0 + b];
+                    int rel;
+                    if (a == 0) rel = x0 + o - pr.i0[0];
+                    else if (a == 1) rel = y0 + o - pr.i0[1];
+                    else rel = imod(z0 + o - pr.i0[2], g.M3);
+                    T w = (rel >= 0 && rel < P) ? wts[(size_t)(b0 + b) * 3 * P + a * P + rel] : (T)0;
+                    if (a == 2) w *= pr.q;
+                    sw[b][a][o] = w;
+                }
+                __syncthreads();
+                for (int b = 0; b < nb; ++b) {
+                    const T s = sw[b][2][tz] * sw[b][1][ty];
+#pragma unroll
+                    for (int c = 0; c < kBin; ++c) acc[c] += s * sw[b][0][c];
+                }
+                __syncthreads();
+            }
+        }
+    }
+    const int z = z0 + tz, y = y0 + ty;
+    if (z < g.M3 && y < g.Mt) {
+        T *dst = grid + ((size_t)z * g.Mt + y) * g.Mt + x0;
+#pragma unroll
+        for (int c = 0; c < kBin; ++c)
+            if (x0 + c < g.Mt) dst[c] = acc[c];
+    }
+}
+
+// ------------------------------------------------------------------ gathering (Eqs. 3.11, 3.25)
+//
+// One warp per particle; lane l handles x offset l of the support (P <= 32),
+// loops over the P x P (z, y) rows with the y and z window values broadcast
+// from shared memory, and the four sums are reduced across the warp.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather(Geo g, int n, const PartRec<T> *__restrict__ parts,
+                                                const T *__restrict__ wts, const T *__restrict__ grid,
+                                                double *__restrict__ phi, double *__restrict__ frc,
+                                                int add_self)
+{
+    __shared__ T sy[8][2][32], sz[8][2][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int P = g.P;
+    const int warps_total = gridDim.x * (blockDim.x >> 5);
+    const T h = (T)g.h, hz = (T)g.hz;
+    for (int pi = blockIdx.x * (blockDim.x >> 5) + wib; pi < n; pi += warps_total) {
+        const PartRec<T> r = parts[pi];
+        const T *w = wts + (size_t)pi * 3 * P;
+        T wx = 0, wxd = 0;
+        if (lane < P) {
+            const T jc = (T)(lane - g.c);
+            wx = w[lane];
+            wxd = wx * (r.g[0] - jc) * h;
+            const T wy = w[P + lane], wz = w[2 * P + lane];
+            sy[wib][0][lane] = wy;
+            sy[wib][1][lane] = wy * (r.g[1] - jc) * h;
+            sz[wib][0][lane] = wz;
+            sz[wib][1][lane] = wz * (r.g[2] - jc) * hz;
+        }
+        __syncwarp();
+        T aphi = 0, afy = 0, afz = 0;
+        if (lane < P) {
+            for (int k = 0; k < P; ++k) {
+                int zk = r.i0[2] + k;
+                if (zk >= g.M3) zk -= g.M3;
+                const T *row = grid + ((size_t)zk * g.Mt + r.i0[1]) * g.Mt + r.i0[0] + lane;
+                T a = 0, b = 0;
+                for (int j = 0; j < P; ++j) {
+                    const T v = __ldg(row + (size_t)j * g.Mt);
+                    a += sy[wib][0][j] * v;
+                    b += sy[wib][1][j] * v;
+                }
+                aphi += sz[wib][0][k] * a;
+                afy += sz[wib][0][k] * b;
+                afz += sz[wib][1][k] * a;
+            }
+        }
+        T vphi = warp_sum(wx * aphi);
+        T vfx = warp_sum(wxd * aphi);
+        T vfy = warp_sum(wx * afy);
+        T vfz = warp_sum(wx * afz);
+        if (lane == 0) {
+            const double h3 = g.h * g.h * g.hz;
+            const double qd = (double)r.q;
+            double ph = h3 * (double)vphi;
+            if (add_self) ph += -2.0 * g.xi / sqrt(kPi) * qd;
+            phi[r.orig] = ph;
+            const double cxy = 4.0 * g.xi * g.xi / g.eta, cz = 4.0 * g.xi * g.xi / g.etaz;
+            frc[3 * r.orig + 0] = qd * h3 * cxy * (double)vfx;
+            frc[3 * r.orig + 1] = qd * h3 * cxy * (double)vfy;
+            frc[3 * r.orig + 2] = qd * h3 * cz * (double)vfz;
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ outputs and energy
+__global__ void k_finalize(int n, const double *__restrict__ xyzq, const double *__restrict__ phi_int,
+                           const double *__restrict__ frc_int, double *__restrict__ phi,
+                           double *__restrict__ frc, double *__restrict__ epart)
+{
+    double e = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double ph = phi_int[i];
+        e += xyzq[4 * i + 3] * ph;
+        if (phi) phi[i] = ph;
+        if (frc) {
+            frc[3 * i] = frc_int[3 * i];
+            frc[3 * i + 1] = frc_int[3 * i + 1];
+            frc[3 * i + 2] = frc_int[3 * i + 2];
+        }
+    }
+    __shared__ double ws[32];
+    e = warp_sum(e);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) epart[blockIdx.x] = v;
+    }
+}
+
+__global__ void k_energy_final(const double *__restrict__ epart, int nparts, double *__restrict__ energy)
+{
+    __shared__ double ws[32];
+    double e = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) e += epart[i];
+    e = warp_sum(e);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) *energy = 0.5 * v;
+    }
+}
+
+template <typename TS, typename TD>
+__global__ void k_convert(size_t n, const TS *__restrict__ src, TD *__restrict__ dst)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = (TD)src[i];
+}
+
+inline int blocks_for(size_t n, int bs, int cap = 1 << 20)
+{
+    size_t b = (n + bs - 1) / bs;
+    if (b < 1) b = 1;
+    return (int)(b > (size_t)cap ? cap : b);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+template <typename T> void launch_pack(se1p_plan *p, int n, const double *x, const double *q, cudaStream_t s)
+{
+    const Geo &g = p->geo;
+    cudaMemsetAsync(p->b.counts, 0, sizeof(int) * (g.nbins + g.ncells), s);
+    cudaMemsetAsync(p->b.sums, 0, sizeof(double) * 2, s);
+    if (n > 0)
+        k_pack<T><<<blocks_for(n, 256), 256, 0, s>>>(g, n, x, q, p->b.xyzq, p->b.bin_key, p->b.cell_key,
+                                                       p->b.counts, p->b.counts + g.nbins, p->b.sums,
+                                                       p->b.status);
+    k_scan<<<2, 1024, 0, s>>>(g.nbins, g.ncells, p->b.counts, p->b.starts, p->b.cursors, p->b.sums,
+                              p->b.status);
+}
+
+template <typename T> void launch_sort_scatter(se1p_plan *p, int n, cudaStream_t s)
+{
+    const Geo &g = p->geo;
+    if (n <= 0) return;
+    k_scatter<T><<<blocks_for(n, 128), 128, 0, s>>>(g, n, p->b.xyzq, p->b.bin_key, p->b.cell_key,
+                                                      p->b.cursors, p->b.cursors + g.nbins,
+                                                      (PartRec<T> *)p->b.parts, (T *)p->b.wts,
+                                                      (CellRec<T> *)p->b.cells);
+}
+
+template <typename T> void launch_spread(se1p_plan *p, cudaStream_t s)
+{
+    const Geo &g = p->geo;
+    const int nt = (g.Mt + kBin - 1) / kBin;
+    const int ntz = (g.M3 + kBin - 1) / kBin;
+    k_spread<T><<<nt * nt * ntz, 64, 0, s>>>(g, p->b.starts, (const PartRec<T> *)p->b.parts,
+                                              (const T *)p->b.wts, (T *)p->b.grid);
+}
+
+template <typename T>
+void launch_gather(se1p_plan *p, int n, const void *grid, double *phi, double *frc, int add_self, cudaStream_t s)
+{
+    if (n <= 0) return;
+    const int warps_per_block = 8;
+    int blocks = (n + warps_per_block - 1) / warps_per_block;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    k_gather<T><<<blocks, 32 * warps_per_block, 0, s>>>(p->geo, n, (const PartRec<T> *)p->b.parts,
+                                                         (const T *)p->b.wts, (const T *)grid, phi, frc,
+                                                         add_self);
+}
+
+void launch_finalize(se1p_plan *p, int n, double *phi, double *frc, double *energy, cudaStream_t s)
+{
+    k_finalize<<<kEnergyBlocks, 256, 0, s>>>(n, p->b.xyzq, p->b.phi_int, p->b.frc_int, phi, frc, p->b.epart);
+    if (energy) k_energy_final<<<1, 256, 0, s>>>(p->b.epart, kEnergyBlocks, energy);
+}
+
+template <typename T> void launch_grid_to_double(se1p_plan *p, const void *src, double *dst, cudaStream_t s)
+{
+    const size_t n = (size_t)p->M3 * p->Mt * p->Mt;
+    k_convert<T, double><<<blocks_for(n, 256, 4096), 256, 0, s>>>(n, (const T *)src, dst);
+}
+
+template <typename T> void launch_grid_from_double(se1p_plan *p, const double *src, void *dst, cudaStream_t s)
+{
+    const size_t n = (size_t)p->M3 * p->Mt * p->Mt;
+    k_convert<double, T><<<blocks_for(n, 256, 4096), 256, 0, s>>>(n, src, (T *)dst);
+}
+
+template <typename T> int configure_particle_kernels() { return 0; }
+
+#define SE1P_INST(T)                                                                                        \
+    template void launch_pack<T>(se1p_plan *, int, const double *, const double *, cudaStream_t);          \
+    template void launch_sort_scatter<T>(se1p_plan *, int, cudaStream_t);                                   \
+    template void launch_spread<T>(se1p_plan *, cudaStream_t);                                              \
+    template void launch_gather<T>(se1p_plan *, int, const void *, double *, double *, int, cudaStream_t);  \
+    template void launch_grid_to_double<T>(se1p_plan *, const void *, double *, cudaStream_t);             \
+    template void launch_grid_from_double<T>(se1p_plan *, const double *, void *, cudaStream_t);           \
+    template int configure_particle_kernels<T>();
+SE1P_INST(float)
+SE1P_INST(double)
+#undef SE1P_INST
+
+}  // namespace se1p

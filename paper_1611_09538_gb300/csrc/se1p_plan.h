@@ -1,0 +1,98 @@
+// Host-side plan object and kernel launchers of libse1p (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include <vector>
+
+#include "se1p_internal.cuh"
+
+namespace se1p {
+
+// One class of k3 slabs sharing a padded 2-D size (k3 = 0, the set I, the set J).
+struct SlabClass {
+    int ns = 0;       // padded 2-D size
+    int kfirst = 0;   // first k3 index of the class
+    int count = 0;    // number of k3 indices
+    FftDesc fd{};     // FFT of length ns
+    void *tw = nullptr;     // twiddles (Cx<T>, or Cx<double> for class 0)
+    void *rows = nullptr;   // [count][Mt][ns] complex work rows
+    void *ex = nullptr;     // exp(-(1-eta) kappa_i^2 / 4 xi^2), i = 0..ns-1 (T)
+    int rb = 1;             // rows per CTA in the x passes
+    int xb = 1;             // columns per CTA in the y pass
+};
+
+struct Buffers {
+    void *grid = nullptr;        // T [M3][Mt][Mt]
+    void *zspec = nullptr;       // Cx<T> [K3][Mt][Mt]  (k3 = 0 entry unused)
+    double *slab0_in = nullptr;  // k3 = 0 coefficient of H, [Mt][Mt]
+    double *slab0_out = nullptr; // k3 = 0 coefficient of Ht, [Mt][Mt]
+    double *sym0 = nullptr;      // k3 = 0 scaling incl. normalisation, [n0][n0]
+    void *ez = nullptr;          // exp(-(1-etaz) k3^2 / 4 xi^2) / (k3 normalisation), [K3] (T)
+    void *tw_z = nullptr;        // Cx<T> [M3]
+    double *xyzq = nullptr;      // sanitised caller-order particles [n_max][4]
+    int *bin_key = nullptr, *cell_key = nullptr;
+    int *counts = nullptr;       // [nbins + ncells]
+    int *starts = nullptr;       // [nbins + 1 + ncells + 1]
+    int *cursors = nullptr;      // [nbins + ncells]
+    void *parts = nullptr;       // PartRec<T> [n_max]
+    void *wts = nullptr;         // T [n_max][3][P]
+    void *cells = nullptr;       // CellRec<T> [n_max]
+    double *phi_int = nullptr;   // [n_max]
+    double *frc_int = nullptr;   // [n_max][3]
+    double *sums = nullptr;      // [2] sum q, sum |q|
+    double *epart = nullptr;     // [kEnergyBlocks]
+    int *status = nullptr;
+    double *hx = nullptr, *hq = nullptr, *hphi = nullptr, *hfrc = nullptr, *hen = nullptr;  // host staging
+    double *dgrid = nullptr;     // FP64 grid for stage entry points [M3][Mt][Mt]
+};
+
+constexpr int kEnergyBlocks = 256;
+
+}  // namespace se1p
+
+struct se1p_plan {
+    se1p_params prm{};
+    se1p::Geo geo{};
+    int n_max = 0;
+    int precision = 0;
+    int device = 0;
+    int Mt = 0, M3 = 0, K3 = 0, n0 = 0, nI = 0, nl = 0;
+    se1p::FftDesc fd_z{};
+    int xb_z = 1;
+    se1p::SlabClass cls[3];  // 0: k3 = 0 (FP64 always), 1: I, 2: J
+    se1p::Buffers b;
+    std::vector<void *> dev_allocs;
+    std::vector<void *> host_allocs;
+    size_t bytes = 0;
+    double norm_k3 = 0;  // 4 pi / M3 (class-specific 1/ns^2 applied in kernels)
+    // per-stage profiling events: [eval][stage boundary]
+    int profiling = 0;
+    int prof_count = 0;
+    std::vector<cudaEvent_t> prof_events;
+};
+
+namespace se1p {
+
+// ---- se1p_particles.cu
+template <typename T> void launch_pack(se1p_plan *p, int n, const double *x, const double *q, cudaStream_t s);
+template <typename T> void launch_sort_scatter(se1p_plan *p, int n, cudaStream_t s);
+template <typename T> void launch_spread(se1p_plan *p, cudaStream_t s);
+template <typename T> void launch_gather(se1p_plan *p, int n, const void *grid, double *phi, double *frc,
+                                         int add_self, cudaStream_t s);
+void launch_finalize(se1p_plan *p, int n, double *phi, double *frc, double *energy, cudaStream_t s);
+template <typename T> void launch_grid_to_double(se1p_plan *p, const void *src, double *dst, cudaStream_t s);
+template <typename T> void launch_grid_from_double(se1p_plan *p, const double *src, void *dst, cudaStream_t s);
+template <typename T> int configure_particle_kernels();
+
+// ---- se1p_fourier.cu
+template <typename T> void launch_fourier(se1p_plan *p, cudaStream_t s);
+template <typename T> int configure_fourier_kernels(se1p_plan *p);
+void launch_vico_table(se1p_plan *p, cudaStream_t s);
+
+// ---- se1p_real.cu
+template <typename T> void launch_real_space(se1p_plan *p, double *phi, double *frc, int accumulate,
+                                             cudaStream_t s);
+
+}  // namespace se1p

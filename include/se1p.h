@@ -174,6 +174,34 @@ se1p_status se1p_plan_stage_times(se1p_plan *plan, double *ms, int *n_evals);
  * error recorded since the last call), then clear it. */
 se1p_status se1p_plan_sync_status(se1p_plan *plan, void *stream);
 
+/* ---- allocation-free variant ----
+ *
+ * se1p_real_space_noalloc: the real-space part (phi^R and F^R, as
+ * se1p_real_space) for callers that cannot allocate device memory, e.g. code
+ * that runs while a framework owns the device allocator, embedded hosts whose
+ * device memory is handed out up front, or plugins in processes that forbid
+ * allocation after start-up.  The paper has no counterpart: this is a
+ * deployment variant of the same sum.
+ *
+ * It takes the parameters directly (no plan: plan creation allocates) and uses
+ * params->L, xi, rc (> 0, <= L3) and precision.  All scratch lives in one
+ * file-scope __device__ array of about 1.7 MB that every GPU which loads the
+ * library holds until the process exits; nothing is allocated or freed (no
+ * cudaMalloc, cudaFree or allocating library routine).
+ *   - n <= 16384 particles (larger n returns SE1P_ERR_CAPACITY); the cell list
+ *     is capped at 4096 cells, made coarser (never finer than rc) if needed.
+ *   - x, q, phi, force are device pointers; phi and force must be non-NULL.
+ *     Writes (does not accumulate) phi and force.  Inputs are sanitised as in
+ *     se1p_eval, but this entry point records no device status.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the array and leaves its contents behind; calls whose
+ *     work overlaps on the GPU race on it and must be serialised by the caller.
+ * Asynchronous on `stream`. */
+se1p_status se1p_real_space_noalloc(const se1p_params *params, int n, const double *x, const double *q,
+                                    double *phi, double *force, void *stream);
+
 /* Static, human-readable name of a status code. */
 const char *se1p_status_string(se1p_status status);
 

@@ -30,7 +30,7 @@ STATUS = {
 EXPORTS = (
     "se1p_plan_create", "se1p_plan_destroy", "se1p_plan_get_info", "se1p_eval", "se1p_eval_host",
     "se1p_spread", "se1p_fourier", "se1p_gather", "se1p_real_space", "se1p_plan_set_profiling",
-    "se1p_plan_stage_times", "se1p_plan_sync_status", "se1p_status_string",
+    "se1p_plan_stage_times", "se1p_plan_sync_status", "se1p_real_space_noalloc", "se1p_status_string",
 )
 
 STAGES = ("pack", "spread", "fourier", "gather", "real", "final")
@@ -86,6 +86,7 @@ def load(path: str | None = None):
     lib.se1p_plan_set_profiling.argtypes = [vp, i]
     lib.se1p_plan_stage_times.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i)]
     lib.se1p_plan_sync_status.argtypes = [vp, vp]
+    lib.se1p_real_space_noalloc.argtypes = [ctypes.POINTER(se1p_params), i, vp, vp, vp, vp, vp]
     lib.se1p_status_string.argtypes = [i]
     lib.se1p_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -198,6 +199,13 @@ def se1p_plan_sync_status(plan, stream=None) -> int:
     return int(load().se1p_plan_sync_status(plan, _stream(stream)))
 
 
+def se1p_real_space_noalloc(params: se1p_params, n, x, q, phi, force, stream=None) -> None:
+    """Real-space sum without any device allocation (scratch in a static device array;
+    n <= 16384; concurrent calls must be serialised by the caller)."""
+    _check(load().se1p_real_space_noalloc(ctypes.byref(params), int(n), _ptr(x), _ptr(q), _ptr(phi),
+                                          _ptr(force), _stream(stream)), "se1p_real_space_noalloc")
+
+
 def se1p_status_string(code: int) -> str:
     return load().se1p_status_string(int(code)).decode()
 
@@ -215,6 +223,7 @@ class Plan:
     """Owns one C plan; evaluates torch CUDA tensors (x [n,3], q [n], float64)."""
 
     def __init__(self, L, xi, M, P, n_max, **kw):
+        """L, xi, M, P as in se1p_params; keywords as make_params."""
         self.params = make_params(L, xi, M, P, **kw)
         self.handle = se1p_plan_create(self.params, n_max)
         self.n_max = n_max

@@ -215,7 +215,7 @@ se1p_status run_eval(se1p_plan *p, int n, const double *x, const double *q, doub
     m.mark(SE1P_STAGE_GATHER);
     launch_gather<T>(p, n, p->b.grid, p->b.phi_int, p->b.frc_int, 1, s);
     m.mark(SE1P_STAGE_REAL);
-    if (p->geo.rc > 0) launch_real_space<T>(p, p->b.phi_int, p->b.frc_int, 1, s);
+    if (p->geo.rc > 0) launch_real_space<T>(p, n, p->b.cell_key, p->b.phi_int, p->b.frc_int, 1, s);
     m.mark(SE1P_STAGE_FINAL);
     launch_finalize(p, n, phi, frc, energy, s);
     m.mark(SE1P_NUM_STAGES);
@@ -326,9 +326,15 @@ se1p_status se1p_plan_create(const se1p_params *prm, int n_max, se1p_plan **out)
     g.rc = P.rc > 0.0 ? P.rc : 0.0;
     g.rc2 = g.rc * g.rc;
     if (g.rc > 0.0) {
-        g.ncx = (int)fmin(fmax(floor(P.L[0] / g.rc), 1.0), 512.0);
-        g.ncy = (int)fmin(fmax(floor(P.L[1] / g.rc), 1.0), 512.0);
-        g.ncz = (int)fmin(fmax(floor(P.L[2] / g.rc), 1.0), 4096.0);
+        // cells of edge >= rc/2 (stencil of +-2 cells), at most 2^22 cells in total
+        const double ce = g.rc / 2.0;
+        g.ncx = (int)fmin(fmax(floor(P.L[0] / ce), 1.0), 1024.0);
+        g.ncy = (int)fmin(fmax(floor(P.L[1] / ce), 1.0), 1024.0);
+        g.ncz = (int)fmin(fmax(floor(P.L[2] / ce), 1.0), 8192.0);
+        while ((long)g.ncx * g.ncy * g.ncz > (1L << 22)) {
+            if (g.ncz >= g.ncx) g.ncz = (g.ncz + 1) / 2;
+            else { g.ncx = (g.ncx + 1) / 2; g.ncy = (g.ncy + 1) / 2; }
+        }
     } else {
         g.ncx = g.ncy = g.ncz = 1;
     }
@@ -351,11 +357,19 @@ se1p_status se1p_plan_create(const se1p_params *prm, int n_max, se1p_plan **out)
 
     const bool mixed = P.precision == SE1P_MIXED;
     const size_t cT = mixed ? sizeof(Cx<float>) : sizeof(Cx<double>);
-    p->xb_z = pow2_fit(2 * (size_t)p->M3 * cT, 32);
+    // pencils per CTA: as many as shared memory allows, but few enough that each
+    // pass launches at least ~2 CTAs per SM (152 SMs)
+    const long min_ctas = 2 * 152;
+    auto shrink = [&](int v, long units) {
+        while (v > 1 && (units + v - 1) / v < min_ctas) v >>= 1;
+        return v;
+    };
+    p->xb_z = shrink(pow2_fit(2 * (size_t)p->M3 * cT, 32), (long)p->Mt * p->Mt);
     for (int c = 0; c < 3; ++c) {
         const size_t cc = c == 0 ? sizeof(Cx<double>) : cT;
-        p->cls[c].rb = pow2_fit(2 * (size_t)p->cls[c].ns * cc, 16);
-        p->cls[c].xb = pow2_fit(2 * (size_t)p->cls[c].ns * cc, 32);
+        SlabClass &C = p->cls[c];
+        C.rb = shrink(pow2_fit(2 * (size_t)C.ns * cc, 16), (long)C.count * p->Mt);
+        C.xb = shrink(pow2_fit(2 * (size_t)C.ns * cc, 32), (long)C.count * C.ns);
     }
     if (2 * (size_t)p->M3 * cT * p->xb_z > 200 * 1024) { delete p; return SE1P_ERR_INVALID_ARG; }
     for (int c = 0; c < 3; ++c) {
@@ -560,11 +574,11 @@ se1p_status se1p_real_space(se1p_plan *p, int n, const double *x, const double *
     if (p->precision == SE1P_MIXED) {
         launch_pack<float>(p, n, x, q, s);
         launch_sort_scatter<float>(p, n, s);
-        launch_real_space<float>(p, p->b.phi_int, p->b.frc_int, 0, s);
+        launch_real_space<float>(p, n, p->b.cell_key, p->b.phi_int, p->b.frc_int, 0, s);
     } else {
         launch_pack<double>(p, n, x, q, s);
         launch_sort_scatter<double>(p, n, s);
-        launch_real_space<double>(p, p->b.phi_int, p->b.frc_int, 0, s);
+        launch_real_space<double>(p, n, p->b.cell_key, p->b.phi_int, p->b.frc_int, 0, s);
     }
     launch_finalize(p, n, phi, force, nullptr, s);
     return check_launch();

@@ -217,14 +217,13 @@ template <typename T> struct PartRec {
     T q;
 };
 
-// Real-space record in cell order: coordinates relative to the cell's lower
-// corner, computed in FP64 and stored as an unevaluated sum hi + lo of two T
-// values (lo = 0 for T = double), charge and caller index.  With FP32 the
-// split keeps close-pair displacements accurate to a few ulps of |d| instead
-// of a few ulps of the cell size.
-template <typename T> struct CellRec {
-    T lx, ly, lz, q;
-    T ex, ey, ez;
+// Real-space record in cell order: absolute coordinates, computed in FP64 and
+// stored as an unevaluated sum hi + lo of two T values (lo = 0 for T = double),
+// charge and caller index.  With FP32 the split keeps pair displacements
+// accurate to a few ulps of |d| instead of a few ulps of the coordinates.
+template <typename T> struct __align__(sizeof(T) == 4 ? 16 : 32) CellRec {
+    T xh, yh, zh, q;
+    T xl, yl, zl;
     int orig;
 };
 

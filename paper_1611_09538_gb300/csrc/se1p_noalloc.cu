@@ -135,16 +135,14 @@ __global__ void k_na_scatter(Geo g, int n, const double *__restrict__ xyzq, cons
     if (i >= n) return;
     const double4 p = reinterpret_cast<const double4 *>(xyzq)[i];
     const int cell = key[i];
-    const int cx = cell % g.ncx, cy = (cell / g.ncx) % g.ncy, cz = cell / (g.ncx * g.ncy);
     const int pos = atomicAdd(cursor + cell, 1);
-    const double lx = p.x - cx * g.cs[0], ly = p.y - cy * g.cs[1], lz = p.z - cz * g.cs[2];
     CellRec<T> c;
-    c.lx = (T)lx;
-    c.ly = (T)ly;
-    c.lz = (T)lz;
-    c.ex = (T)(lx - (double)c.lx);
-    c.ey = (T)(ly - (double)c.ly);
-    c.ez = (T)(lz - (double)c.lz);
+    c.xh = (T)p.x;
+    c.yh = (T)p.y;
+    c.zh = (T)p.z;
+    c.xl = (T)(p.x - (double)c.xh);
+    c.yl = (T)(p.y - (double)c.yh);
+    c.zl = (T)(p.z - (double)c.zh);
     c.q = (T)p.w;
     c.orig = i;
     cells[pos] = c;
@@ -173,7 +171,7 @@ se1p_status na_run(const se1p_params &P, const Geo &g, unsigned char *scr, int n
     view.geo = g;
     view.b.starts = starts;  // cell starts begin at starts + nbins + 1 = starts + 1
     view.b.cells = cells;
-    launch_real_space<T>(&view, phi, force, 0, s);
+    launch_real_space<T>(&view, n, key, phi, force, 0, s);
     return cudaGetLastError() == cudaSuccess ? SE1P_OK : SE1P_ERR_CUDA;
 }
 

@@ -189,18 +189,16 @@ __global__ void k_scatter(Geo g, int n, const double *__restrict__ xyzq, const i
         }
     }
     parts[pos] = r;
-    // cell order, coordinates relative to the cell corner (FP64 difference, stored in T)
+    // cell order, absolute coordinates as hi + lo
     const int cell = cell_key[i];
-    const int cx = cell % g.ncx, cy = (cell / g.ncx) % g.ncy, cz = cell / (g.ncx * g.ncy);
     const int cpos = atomicAdd(cell_cursor + cell, 1);
     CellRec<T> c;
-    const double lx = p.x - cx * g.cs[0], ly = p.y - cy * g.cs[1], lz = p.z - cz * g.cs[2];
-    c.lx = (T)lx;
-    c.ly = (T)ly;
-    c.lz = (T)lz;
-    c.ex = (T)(lx - (double)c.lx);
-    c.ey = (T)(ly - (double)c.ly);
-    c.ez = (T)(lz - (double)c.lz);
+    c.xh = (T)p.x;
+    c.yh = (T)p.y;
+    c.zh = (T)p.z;
+    c.xl = (T)(p.x - (double)c.xh);
+    c.yl = (T)(p.y - (double)c.yh);
+    c.zl = (T)(p.z - (double)c.zh);
     c.q = (T)p.w;
     c.orig = i;
     cells[cpos] = c;
@@ -209,33 +207,46 @@ __global__ void k_scatter(Geo g, int n, const double *__restrict__ xyzq, const i
 // ------------------------------------------------------------------ gridding (Eq. 3.4)
 //
 // Output-stationary: one CTA owns an 8x8x8 tile of the grid and accumulates
-// every particle whose support overlaps it in registers (no atomics); thread
-// (tz, ty) owns the 8 x-points of one row.  Particles are visited bin by bin
-// (bins of 8 support-start indices per axis), staged 32 at a time as their
-// window values at the tile's 8 offsets per axis (zero outside the support).
-constexpr int kSpreadBatch = 32;
+// every particle whose support overlaps it in registers (no atomics; every
+// grid point is written exactly once).  A 16-thread group covers the tile with
+// 2(z) x 2(y) x 8(x) points per thread, so each particle costs a thread 4
+// shared loads (its z, y and x window values) for 32 FMAs; the CTA's eight
+// groups take alternate particles and their partial tiles are added at the end.
+// Particles are visited bin by bin (bins of 8 support-start indices per axis).
+// A batch of 128 records is loaded once into shared memory, then one thread
+// per (particle, axis) gathers the window values at the tile's 8 offsets
+// (zero outside the support, charge folded into z).
+constexpr int kSpreadBatch = 128;
+constexpr int kSpreadGroups = 8;
+constexpr int kSpreadThreads = 16 * kSpreadGroups;
 
 template <typename T>
-__global__ void __launch_bounds__(64) k_spread(Geo g, const int *__restrict__ bin_start,
-                                               const PartRec<T> *__restrict__ parts,
-                                               const T *__restrict__ wts, T *__restrict__ grid)
+__global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int *__restrict__ bin_start,
+                                                           const PartRec<T> *__restrict__ parts,
+                                                           const T *__restrict__ wts, T *__restrict__ grid)
 {
-    __shared__ T sw[kSpreadBatch][3][kBin];
+    __shared__ __align__(16) T sw[kSpreadBatch][3][kBin];
+    __shared__ int soff[kSpreadBatch][3];
+    __shared__ T sq[kSpreadBatch];
+    __shared__ __align__(16) T red[kSpreadGroups - 1][16][4][kBin];
     const int ntx = (g.Mt + kBin - 1) / kBin, nty = ntx;
     const int tile = blockIdx.x;
     const int txi = tile % ntx, tyi = (tile / ntx) % nty, tzi = tile / (ntx * nty);
     const int x0 = txi * kBin, y0 = tyi * kBin, z0 = tzi * kBin;
-    const int tz = threadIdx.x >> 3, ty = threadIdx.x & 7;
-    const int P = g.P;
-    T acc[kBin];
+    const int grp = threadIdx.x >> 4, tl = threadIdx.x & 15;
+    const int tz = 2 * (tl >> 2), ty = 2 * (tl & 3);  // this thread's z and y pairs
+    const int P = g.P, M3 = g.M3;
+    T acc[4][kBin];  // [2 dz + dy][x]
 #pragma unroll
-    for (int c = 0; c < kBin; ++c) acc[c] = (T)0;
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < kBin; ++c) acc[r][c] = (T)0;
 
     // bins whose start indices can reach the tile
     const int bx_lo = max(x0 - P + 1, 0) / kBin, bx_hi = min(x0 + kBin - 1, g.Mt - P) / kBin;
     const int by_lo = max(y0 - P + 1, 0) / kBin, by_hi = min(y0 + kBin - 1, g.Mt - P) / kBin;
     const int span = P + kBin - 1;  // cyclic range of z starts [z0-P+1, z0+7]
-    const bool allz = span + 2 * kBin > g.M3;
+    const bool allz = span + 2 * kBin > M3;
     int u = 0;
     int zb_iter = 0;
     while (true) {
@@ -245,9 +256,11 @@ __global__ void __launch_bounds__(64) k_spread(Geo g, const int *__restrict__ bi
             bz = zb_iter++;
         } else {
             if (u >= span) break;
-            const int s = imod(z0 - P + 1 + u, g.M3);
+            int s = z0 - P + 1 + u;
+            if (s < 0) s += M3;
+            if (s >= M3) s -= M3;
             bz = s / kBin;
-            u += min((bz + 1) * kBin, g.M3) - s;
+            u += min((bz + 1) * kBin, M3) - s;
         }
         if (bx_lo > bx_hi || by_lo > by_hi) continue;
         for (int by = by_lo; by <= by_hi; ++by) {
@@ -255,33 +268,74 @@ __global__ void __launch_bounds__(64) k_spread(Geo g, const int *__restrict__ bi
             const int beg = bin_start[row + bx_lo], end = bin_start[row + bx_hi + 1];
             for (int b0 = beg; b0 < end; b0 += kSpreadBatch) {
                 const int nb = min(kSpreadBatch, end - b0);
-                for (int e = threadIdx.x; e < nb * 3 * kBin; e += blockDim.x) {
-                    const int b = e / (3 * kBin), r = e % (3 * kBin), a = r / kBin, o = r % kBin;
-                    const PartRec<T> &pr = parts[b0 + b];
-                    int rel;
-                    if (a == 0) rel = x0 + o - pr.i0[0];
-                    else if (a == 1) rel = y0 + o - pr.i0[1];
-                    else rel = imod(z0 + o - pr.i0[2], g.M3);
-                    T w = (rel >= 0 && rel < P) ? wts[(size_t)(b0 + b) * 3 * P + a * P + rel] : (T)0;
-                    if (a == 2) w *= pr.q;
-                    sw[b][a][o] = w;
+                __syncthreads();  // previous batch fully consumed
+                for (int b = threadIdx.x; b < nb; b += kSpreadThreads) {
+                    const PartRec<T> pr = parts[b0 + b];
+                    // support offset of the tile origin per axis; z taken cyclically into [-8, M3-9]
+                    int dz = z0 - pr.i0[2];
+                    if (dz < -kBin) dz += M3;
+                    soff[b][0] = x0 - pr.i0[0];
+                    soff[b][1] = y0 - pr.i0[1];
+                    soff[b][2] = dz;
+                    sq[b] = pr.q;
                 }
                 __syncthreads();
-                for (int b = 0; b < nb; ++b) {
-                    const T s = sw[b][2][tz] * sw[b][1][ty];
+                // window values at the tile's 8 offsets: one thread per (particle, axis)
+                for (int e = threadIdx.x; e < nb * 3; e += kSpreadThreads) {
+                    const int b = e / 3, a = e - 3 * b;
+                    const T *wrow = wts + (size_t)(b0 + b) * 3 * P + a * P;
+                    const int base = soff[b][a];
+                    const T scale = a == 2 ? sq[b] : (T)1;
+                    T v[kBin];
 #pragma unroll
-                    for (int c = 0; c < kBin; ++c) acc[c] += s * sw[b][0][c];
+                    for (int o = 0; o < kBin; ++o) {
+                        int rel = base + o;
+                        if (a == 2 && rel >= M3) rel -= M3;
+                        v[o] = (rel >= 0 && rel < P) ? wrow[rel] * scale : (T)0;
+                    }
+#pragma unroll
+                    for (int o = 0; o < kBin; ++o) sw[b][a][o] = v[o];
                 }
                 __syncthreads();
+                for (int b = grp; b < nb; b += kSpreadGroups) {
+                    const T wz0 = sw[b][2][tz], wz1 = sw[b][2][tz + 1];
+                    const T wy0 = sw[b][1][ty], wy1 = sw[b][1][ty + 1];
+                    const T s00 = wz0 * wy0, s01 = wz0 * wy1, s10 = wz1 * wy0, s11 = wz1 * wy1;
+#pragma unroll
+                    for (int c = 0; c < kBin; ++c) {
+                        const T wx = sw[b][0][c];
+                        acc[0][c] += s00 * wx;
+                        acc[1][c] += s01 * wx;
+                        acc[2][c] += s10 * wx;
+                        acc[3][c] += s11 * wx;
+                    }
+                }
             }
         }
     }
-    const int z = z0 + tz, y = y0 + ty;
-    if (z < g.M3 && y < g.Mt) {
-        T *dst = grid + ((size_t)z * g.Mt + y) * g.Mt + x0;
+    __syncthreads();
+    if (grp > 0) {
 #pragma unroll
-        for (int c = 0; c < kBin; ++c)
-            if (x0 + c < g.Mt) dst[c] = acc[c];
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < kBin; ++c) red[grp - 1][tl][r][c] = acc[r][c];
+    }
+    __syncthreads();
+    if (grp == 0) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int z = z0 + tz + (r >> 1), y = y0 + ty + (r & 1);
+            if (z < M3 && y < g.Mt) {
+                T *dst = grid + ((size_t)z * g.Mt + y) * g.Mt + x0;
+#pragma unroll
+                for (int c = 0; c < kBin; ++c) {
+                    T v = acc[r][c];
+#pragma unroll
+                    for (int q = 0; q < kSpreadGroups - 1; ++q) v += red[q][tl][r][c];
+                    if (x0 + c < g.Mt) dst[c] = v;
+                }
+            }
+        }
     }
 }
 
@@ -290,7 +344,7 @@ __global__ void __launch_bounds__(64) k_spread(Geo g, const int *__restrict__ bi
 // One warp per particle; lane l handles x offset l of the support (P <= 32),
 // loops over the P x P (z, y) rows with the y and z window values broadcast
 // from shared memory, and the four sums are reduced across the warp.
-template <typename T>
+template <typename T, int PC>
 __global__ void __launch_bounds__(256) k_gather(Geo g, int n, const PartRec<T> *__restrict__ parts,
                                                 const T *__restrict__ wts, const T *__restrict__ grid,
                                                 double *__restrict__ phi, double *__restrict__ frc,
@@ -298,7 +352,7 @@ __global__ void __launch_bounds__(256) k_gather(Geo g, int n, const PartRec<T> *
 {
     __shared__ T sy[8][2][32], sz[8][2][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int P = g.P;
+    const int P = PC > 0 ? PC : g.P;  // compile-time support width when PC > 0 (loops unroll)
     const int warps_total = gridDim.x * (blockDim.x >> 5);
     const T h = (T)g.h, hz = (T)g.hz;
     for (int pi = blockIdx.x * (blockDim.x >> 5) + wib; pi < n; pi += warps_total) {
@@ -323,6 +377,7 @@ __global__ void __launch_bounds__(256) k_gather(Geo g, int n, const PartRec<T> *
                 if (zk >= g.M3) zk -= g.M3;
                 const T *row = grid + ((size_t)zk * g.Mt + r.i0[1]) * g.Mt + r.i0[0] + lane;
                 T a = 0, b = 0;
+#pragma unroll(PC > 0 ? PC : 1)
                 for (int j = 0; j < P; ++j) {
                     const T v = __ldg(row + (size_t)j * g.Mt);
                     a += sy[wib][0][j] * v;
@@ -439,7 +494,7 @@ template <typename T> void launch_spread(se1p_plan *p, cudaStream_t s)
     const Geo &g = p->geo;
     const int nt = (g.Mt + kBin - 1) / kBin;
     const int ntz = (g.M3 + kBin - 1) / kBin;
-    k_spread<T><<<nt * nt * ntz, 64, 0, s>>>(g, p->b.starts, (const PartRec<T> *)p->b.parts,
+    k_spread<T><<<nt * nt * ntz, kSpreadThreads, 0, s>>>(g, p->b.starts, (const PartRec<T> *)p->b.parts,
                                               (const T *)p->b.wts, (T *)p->b.grid);
 }
 
@@ -450,9 +505,14 @@ void launch_gather(se1p_plan *p, int n, const void *grid, double *phi, double *f
     const int warps_per_block = 8;
     int blocks = (n + warps_per_block - 1) / warps_per_block;
     if (blocks > 152 * 64) blocks = 152 * 64;
-    k_gather<T><<<blocks, 32 * warps_per_block, 0, s>>>(p->geo, n, (const PartRec<T> *)p->b.parts,
-                                                         (const T *)p->b.wts, (const T *)grid, phi, frc,
-                                                         add_self);
+    const Geo &g = p->geo;
+    const PartRec<T> *pr = (const PartRec<T> *)p->b.parts;
+    const T *w = (const T *)p->b.wts;
+    const T *gr = (const T *)grid;
+    const int nt = 32 * warps_per_block;
+    if (g.P == 24) k_gather<T, 24><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, add_self);
+    else if (g.P == 16) k_gather<T, 16><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, add_self);
+    else k_gather<T, 0><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, add_self);
 }
 
 void launch_finalize(se1p_plan *p, int n, double *phi, double *frc, double *energy, cudaStream_t s)

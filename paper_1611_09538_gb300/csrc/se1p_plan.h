@@ -92,7 +92,7 @@ template <typename T> int configure_fourier_kernels(se1p_plan *p);
 void launch_vico_table(se1p_plan *p, cudaStream_t s);
 
 // ---- se1p_real.cu
-template <typename T> void launch_real_space(se1p_plan *p, double *phi, double *frc, int accumulate,
-                                             cudaStream_t s);
+template <typename T> void launch_real_space(se1p_plan *p, int n, const int *cell_key, double *phi, double *frc,
+                                             int accumulate, cudaStream_t s);
 
 }  // namespace se1p

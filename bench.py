@@ -156,12 +156,17 @@ def rel_rms(a, b):
 
 
 # ------------------------------------------------------------------ roofline bookkeeping
-def kernel_source_hash():
+KERNEL_SOURCES = {"k_real": "se1p_real.cu", "k_spread": "se1p_particles.cu", "k_gather": "se1p_particles.cu"}
+
+
+def kernel_source_hash(kernel):
+    """Hash of the source file that defines `kernel` plus the shared internal headers."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1611_09538_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
+    for name in (KERNEL_SOURCES.get(kernel, ""), "se1p_internal.cuh", "se1p_plan.h"):
+        path = os.path.join(csrc, name)
+        if name and os.path.exists(path):
+            with open(path, "rb") as f:
                 h.update(f.read())
     return h.hexdigest()[:16]
 
@@ -175,7 +180,7 @@ def committed_traffic(kernel, workload_name):
     except (OSError, ValueError):
         return None
     ent = t.get(f"{kernel}@{workload_name}")
-    if not ent or ent.get("source_hash") != kernel_source_hash():
+    if not ent or ent.get("source_hash") != kernel_source_hash(kernel):
         return None
     return ent.get("dram_bytes_per_launch")
 

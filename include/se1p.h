@@ -121,6 +121,22 @@ se1p_status se1p_eval(se1p_plan *plan, int n, const double *x, const double *q, 
 se1p_status se1p_eval_host(se1p_plan *plan, int n, const double *x, const double *q,
                            double *phi, double *force, double *energy, void *stream);
 
+/* Adjoint (vector-Jacobian product) of phi, for reverse-mode differentiation.
+ * Given the cotangent v_phi = dl/dphi of a loss l(phi), returns
+ *   grad_q[n]    = dl/dq_n = phi[v](x_n)              (the method applied to charges v)
+ *   grad_x[n][3] = dl/dx_n = -(v_n E[q](x_n) + q_n E[v](x_n)),   E = -grad phi (target side)
+ * exactly for the discrete SE1P operator: gridding and gathering use the same
+ * window (Eqs. 3.4, 3.11), so phi_m = sum_n q_n K(x_m, x_n) with K symmetric and
+ * the source-side derivative equals the target-side one with the roles swapped
+ * (Eq. 3.25 gives the latter); the real-space kernel is symmetric as well.
+ * The grid is recomputed for q and for v (two evaluations), never stored.
+ * v_phi need not be neutral; since phi of a neutral system is defined only for
+ * neutral charge changes, grad_q is meaningful up to a constant shift.
+ * Either output may be NULL.  Device pointers; asynchronous on `stream`.
+ * Energy gradients need no adjoint: dU/dq = phi and dU/dx = -F (se1p_eval). */
+se1p_status se1p_eval_vjp(se1p_plan *plan, int n, const double *x, const double *q, const double *v_phi,
+                          double *grad_x, double *grad_q, void *stream);
+
 /* ---- single steps, for verification of one stage at a time (device pointers) ---- */
 
 /* Gridding, Algorithm 1 step 2 (Eq. 3.4): H on the M3 x Mt x Mt grid, written

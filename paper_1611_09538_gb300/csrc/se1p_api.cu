@@ -162,6 +162,8 @@ template <typename T> se1p_status alloc_particles(se1p_plan *p, Alloc &A)
     p->b.cells = A.dev(sizeof(CellRec<T>) * (size_t)nm);
     p->b.phi_int = (double *)A.dev(sizeof(double) * (size_t)nm);
     p->b.frc_int = (double *)A.dev(sizeof(double) * 3 * (size_t)nm);
+    p->b.phi2 = (double *)A.dev(sizeof(double) * (size_t)nm);
+    p->b.frc2 = (double *)A.dev(sizeof(double) * 3 * (size_t)nm);
     p->b.sums = (double *)A.dev(sizeof(double) * 2);
     p->b.epart = (double *)A.dev(sizeof(double) * kEnergyBlocks);
     p->b.status = (int *)A.dev(sizeof(int));
@@ -200,26 +202,45 @@ struct StageMarks {
     }
 };
 
+// One evaluation of phi (with the self term) and of the force (field = 0) or the
+// field -grad phi (field = 1) for charges q at positions x, into phi / frc.
+template <typename T>
+void run_pass(se1p_plan *p, int n, const double *x, const double *q, double *phi, double *frc, int field,
+              int check_neutral, cudaStream_t s, StageMarks *m)
+{
+    if (m) m->mark(SE1P_STAGE_PACK);
+    launch_pack<T>(p, n, x, q, s, check_neutral);
+    launch_sort_scatter<T>(p, n, s);
+    if (m) m->mark(SE1P_STAGE_SPREAD);
+    launch_spread<T>(p, s);
+    if (m) m->mark(SE1P_STAGE_FOURIER);
+    launch_fourier<T>(p, s);
+    if (m) m->mark(SE1P_STAGE_GATHER);
+    launch_gather<T>(p, n, p->b.grid, phi, frc, 1 | (field ? 2 : 0), s);
+    if (m) m->mark(SE1P_STAGE_REAL);
+    if (p->geo.rc > 0) launch_real_space<T>(p, n, p->b.cell_key, phi, frc, 1 | (field ? 2 : 0), s);
+}
+
 template <typename T>
 se1p_status run_eval(se1p_plan *p, int n, const double *x, const double *q, double *phi, double *frc,
                      double *energy, cudaStream_t s)
 {
     StageMarks m(p, s);
-    m.mark(SE1P_STAGE_PACK);
-    launch_pack<T>(p, n, x, q, s);
-    launch_sort_scatter<T>(p, n, s);
-    m.mark(SE1P_STAGE_SPREAD);
-    launch_spread<T>(p, s);
-    m.mark(SE1P_STAGE_FOURIER);
-    launch_fourier<T>(p, s);
-    m.mark(SE1P_STAGE_GATHER);
-    launch_gather<T>(p, n, p->b.grid, p->b.phi_int, p->b.frc_int, 1, s);
-    m.mark(SE1P_STAGE_REAL);
-    if (p->geo.rc > 0) launch_real_space<T>(p, n, p->b.cell_key, p->b.phi_int, p->b.frc_int, 1, s);
+    run_pass<T>(p, n, x, q, p->b.phi_int, p->b.frc_int, 0, 1, s, &m);
     m.mark(SE1P_STAGE_FINAL);
     launch_finalize(p, n, phi, frc, energy, s);
     m.mark(SE1P_NUM_STAGES);
     m.done();
+    return check_launch();
+}
+
+template <typename T>
+se1p_status run_vjp(se1p_plan *p, int n, const double *x, const double *q, const double *v, double *grad_x,
+                    double *grad_q, cudaStream_t s)
+{
+    run_pass<T>(p, n, x, q, p->b.phi2, p->b.frc2, 1, 1, s, nullptr);      // E[q]
+    run_pass<T>(p, n, x, v, p->b.phi_int, p->b.frc_int, 1, 0, s, nullptr);  // phi[v], E[v]
+    launch_vjp_combine(n, q, v, p->b.frc2, p->b.phi_int, p->b.frc_int, grad_x, grad_q, s);
     return check_launch();
 }
 
@@ -316,6 +337,8 @@ se1p_status se1p_plan_create(const se1p_params *prm, int n_max, se1p_plan **out)
     g.h = P.L[0] / P.M[0];
     g.hz = P.L[2] / P.M[2];
     g.off = P.P * g.h / 2.0;
+    g.inv_h = 1.0 / g.h;
+    g.inv_hz = 1.0 / g.hz;
     g.xi = P.xi;
     g.eta = P.P * P.xi * P.xi * g.h * g.h / (kShapeC * kShapeC * kPi);     // Eq. 3.3
     g.etaz = P.P * P.xi * P.xi * g.hz * g.hz / (kShapeC * kShapeC * kPi);
@@ -477,6 +500,16 @@ se1p_status se1p_plan_stage_times(se1p_plan *p, double *ms, int *n_evals)
     if (n_evals) *n_evals = p->prof_count;
     p->prof_count = 0;
     return SE1P_OK;
+}
+
+se1p_status se1p_eval_vjp(se1p_plan *p, int n, const double *x, const double *q, const double *v_phi,
+                          double *grad_x, double *grad_q, void *stream)
+{
+    if (!p || bad_n(p, n) || (n > 0 && (!x || !q || !v_phi))) return SE1P_ERR_INVALID_ARG;
+    if (n == 0) return SE1P_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    return p->precision == SE1P_MIXED ? run_vjp<float>(p, n, x, q, v_phi, grad_x, grad_q, s)
+                                      : run_vjp<double>(p, n, x, q, v_phi, grad_x, grad_q, s);
 }
 
 se1p_status se1p_plan_sync_status(se1p_plan *p, void *stream)

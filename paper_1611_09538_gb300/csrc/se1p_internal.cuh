@@ -235,6 +235,7 @@ struct Geo {
     int ncx, ncy, ncz, ncells; // real-space cells
     double L[3];
     double h, hz, off;         // spacings, free-axis grid origin shift P h / 2
+    double inv_h, inv_hz;      // 1/h, 1/hz
     double xi, eta, etaz;
     double wnorm_xy, wnorm_z;  // (2 xi^2 / (pi eta))^{1/2} per axis
     double alpha_xy, alpha_z;  // 2 xi^2 h^2 / eta per axis (exponent scale in grid units)

@@ -40,10 +40,11 @@ struct Support {
 __device__ __forceinline__ Support particle_support(const Geo &g, double px, double py, double pz)
 {
     Support s;
-    const double xs = px + g.off, ys = py + g.off;
-    s.t[0] = xs / g.h;
-    s.t[1] = ys / g.h;
-    s.t[2] = pz / g.hz;
+    // grid coordinates (multiplication by 1/h: FP64 division is slow on this part; a
+    // support start can differ from x/h only when t is within an ulp of an integer)
+    s.t[0] = (px + g.off) * g.inv_h;
+    s.t[1] = (py + g.off) * g.inv_h;
+    s.t[2] = pz * g.inv_hz;
     const int hi = g.Mt - g.P;
     s.i0[0] = min(max(support_start(s.t[0], g.P), 0), hi);
     s.i0[1] = min(max(support_start(s.t[1], g.P), 0), hi);
@@ -106,7 +107,8 @@ __global__ void k_pack(Geo g, int n, const double *__restrict__ x, const double 
 // Exclusive scans of the bin and cell histograms (one block per array); the
 // first block also checks neutrality, |sum q| <= 1e-12 sum |q| (Section 2.1).
 __global__ void k_scan(int nbins, int ncells, const int *__restrict__ counts, int *__restrict__ starts,
-                       int *__restrict__ cursors, const double *__restrict__ sums, int *__restrict__ status)
+                       int *__restrict__ cursors, const double *__restrict__ sums, int *__restrict__ status,
+                       int check_neutral)
 {
     const int which = blockIdx.x;
     const int len = which == 0 ? nbins : ncells;
@@ -150,7 +152,7 @@ __global__ void k_scan(int nbins, int ncells, const int *__restrict__ counts, in
         __syncthreads();
     }
     if (threadIdx.x == 0) st[len] = carry;
-    if (which == 0 && threadIdx.x == 0) {
+    if (which == 0 && threadIdx.x == 0 && check_neutral) {
         if (fabs(sums[0]) > 1e-12 * sums[1]) atomicOr(status, FLAG_NOT_NEUTRAL);
     }
 }
@@ -179,12 +181,18 @@ __global__ void k_scatter(Geo g, int n, const double *__restrict__ xyzq, const i
         r.g[a] = (T)gg;
         const double alpha = a < 2 ? g.alpha_xy : g.alpha_z;
         const double wn = a < 2 ? g.wnorm_xy : g.wnorm_z;
-        for (int j = 0; j < g.P; ++j) {
-            const double d = gg - (double)(j - g.c);
-            if (sizeof(T) == sizeof(double)) {
-                w[a * g.P + j] = (T)(wn * exp(-alpha * d * d));
-            } else {
-                w[a * g.P + j] = (T)wn * expf((float)(-alpha * d * d));
+        if constexpr (sizeof(T) == sizeof(double)) {
+            for (int j = 0; j < g.P; ++j) {
+                const double d = gg - (double)(j - g.c);
+                w[a * g.P + j] = wn * exp(-alpha * d * d);
+            }
+        } else {
+            // FP32 window: |gg| < 1, so gg - (j - c) is exact to ~6e-8 absolute and the
+            // exponent's relative error stays below 4e-7 even at the support edge
+            const float gf = (float)gg, af = (float)alpha, wf = (float)wn;
+            for (int j = 0; j < g.P; ++j) {
+                const float d = gf - (float)(j - g.c);
+                w[a * g.P + j] = wf * expf(-af * d * d);
             }
         }
     }
@@ -348,8 +356,10 @@ template <typename T, int PC>
 __global__ void __launch_bounds__(256) k_gather(Geo g, int n, const PartRec<T> *__restrict__ parts,
                                                 const T *__restrict__ wts, const T *__restrict__ grid,
                                                 double *__restrict__ phi, double *__restrict__ frc,
-                                                int add_self)
+                                                int flags)
 {
+    // flags: bit 0 adds the self term (Eq. 2.5); bit 1 writes the field -grad phi
+    // instead of the force -q grad phi
     __shared__ T sy[8][2][32], sz[8][2][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int P = PC > 0 ? PC : g.P;  // compile-time support width when PC > 0 (loops unroll)
@@ -396,12 +406,13 @@ __global__ void __launch_bounds__(256) k_gather(Geo g, int n, const PartRec<T> *
             const double h3 = g.h * g.h * g.hz;
             const double qd = (double)r.q;
             double ph = h3 * (double)vphi;
-            if (add_self) ph += -2.0 * g.xi / sqrt(kPi) * qd;
+            if (flags & 1) ph += -2.0 * g.xi / sqrt(kPi) * qd;
             phi[r.orig] = ph;
             const double cxy = 4.0 * g.xi * g.xi / g.eta, cz = 4.0 * g.xi * g.xi / g.etaz;
-            frc[3 * r.orig + 0] = qd * h3 * cxy * (double)vfx;
-            frc[3 * r.orig + 1] = qd * h3 * cxy * (double)vfy;
-            frc[3 * r.orig + 2] = qd * h3 * cz * (double)vfz;
+            const double qf = (flags & 2) ? 1.0 : qd;
+            frc[3 * r.orig + 0] = qf * h3 * cxy * (double)vfx;
+            frc[3 * r.orig + 1] = qf * h3 * cxy * (double)vfy;
+            frc[3 * r.orig + 2] = qf * h3 * cz * (double)vfz;
         }
         __syncwarp();
     }
@@ -449,6 +460,22 @@ __global__ void k_energy_final(const double *__restrict__ epart, int nparts, dou
     }
 }
 
+// Adjoint of phi (see se1p_eval_vjp): grad_q = phi[v], grad_x = -(v E[q] + q E[v]).
+__global__ void k_vjp_combine(int n, const double *__restrict__ q, const double *__restrict__ v,
+                              const double *__restrict__ Eq, const double *__restrict__ phiv,
+                              const double *__restrict__ Ev, double *__restrict__ grad_x,
+                              double *__restrict__ grad_q)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (grad_q) grad_q[i] = phiv[i];
+    if (grad_x) {
+        const double vi = v[i], qi = q[i];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) grad_x[3 * i + d] = -(vi * Eq[3 * i + d] + qi * Ev[3 * i + d]);
+    }
+}
+
 template <typename TS, typename TD>
 __global__ void k_convert(size_t n, const TS *__restrict__ src, TD *__restrict__ dst)
 {
@@ -466,7 +493,8 @@ inline int blocks_for(size_t n, int bs, int cap = 1 << 20)
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
-template <typename T> void launch_pack(se1p_plan *p, int n, const double *x, const double *q, cudaStream_t s)
+template <typename T>
+void launch_pack(se1p_plan *p, int n, const double *x, const double *q, cudaStream_t s, int check_neutral)
 {
     const Geo &g = p->geo;
     cudaMemsetAsync(p->b.counts, 0, sizeof(int) * (g.nbins + g.ncells), s);
@@ -476,7 +504,7 @@ template <typename T> void launch_pack(se1p_plan *p, int n, const double *x, con
                                                        p->b.counts, p->b.counts + g.nbins, p->b.sums,
                                                        p->b.status);
     k_scan<<<2, 1024, 0, s>>>(g.nbins, g.ncells, p->b.counts, p->b.starts, p->b.cursors, p->b.sums,
-                              p->b.status);
+                              p->b.status, check_neutral);
 }
 
 template <typename T> void launch_sort_scatter(se1p_plan *p, int n, cudaStream_t s)
@@ -499,7 +527,7 @@ template <typename T> void launch_spread(se1p_plan *p, cudaStream_t s)
 }
 
 template <typename T>
-void launch_gather(se1p_plan *p, int n, const void *grid, double *phi, double *frc, int add_self, cudaStream_t s)
+void launch_gather(se1p_plan *p, int n, const void *grid, double *phi, double *frc, int flags, cudaStream_t s)
 {
     if (n <= 0) return;
     const int warps_per_block = 8;
@@ -510,9 +538,15 @@ void launch_gather(se1p_plan *p, int n, const void *grid, double *phi, double *f
     const T *w = (const T *)p->b.wts;
     const T *gr = (const T *)grid;
     const int nt = 32 * warps_per_block;
-    if (g.P == 24) k_gather<T, 24><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, add_self);
-    else if (g.P == 16) k_gather<T, 16><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, add_self);
-    else k_gather<T, 0><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, add_self);
+    if (g.P == 24) k_gather<T, 24><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags);
+    else if (g.P == 16) k_gather<T, 16><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags);
+    else k_gather<T, 0><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags);
+}
+
+void launch_vjp_combine(int n, const double *q, const double *v, const double *Eq, const double *phiv,
+                        const double *Ev, double *grad_x, double *grad_q, cudaStream_t s)
+{
+    if (n > 0) k_vjp_combine<<<blocks_for(n, 256), 256, 0, s>>>(n, q, v, Eq, phiv, Ev, grad_x, grad_q);
 }
 
 void launch_finalize(se1p_plan *p, int n, double *phi, double *frc, double *energy, cudaStream_t s)
@@ -536,7 +570,7 @@ template <typename T> void launch_grid_from_double(se1p_plan *p, const double *s
 template <typename T> int configure_particle_kernels() { return 0; }
 
 #define SE1P_INST(T)                                                                                        \
-    template void launch_pack<T>(se1p_plan *, int, const double *, const double *, cudaStream_t);          \
+    template void launch_pack<T>(se1p_plan *, int, const double *, const double *, cudaStream_t, int);     \
     template void launch_sort_scatter<T>(se1p_plan *, int, cudaStream_t);                                   \
     template void launch_spread<T>(se1p_plan *, cudaStream_t);                                              \
     template void launch_gather<T>(se1p_plan *, int, const void *, double *, double *, int, cudaStream_t);  \

@@ -41,6 +41,8 @@ struct Buffers {
     void *cells = nullptr;       // CellRec<T> [n_max]
     double *phi_int = nullptr;   // [n_max]
     double *frc_int = nullptr;   // [n_max][3]
+    double *phi2 = nullptr;      // [n_max]     second evaluation of the adjoint
+    double *frc2 = nullptr;      // [n_max][3]
     double *sums = nullptr;      // [2] sum q, sum |q|
     double *epart = nullptr;     // [kEnergyBlocks]
     int *status = nullptr;
@@ -76,11 +78,15 @@ struct se1p_plan {
 namespace se1p {
 
 // ---- se1p_particles.cu
-template <typename T> void launch_pack(se1p_plan *p, int n, const double *x, const double *q, cudaStream_t s);
+template <typename T>
+void launch_pack(se1p_plan *p, int n, const double *x, const double *q, cudaStream_t s, int check_neutral = 1);
 template <typename T> void launch_sort_scatter(se1p_plan *p, int n, cudaStream_t s);
 template <typename T> void launch_spread(se1p_plan *p, cudaStream_t s);
+// flags: bit 0 adds the self term, bit 1 writes the field -grad phi instead of the force
 template <typename T> void launch_gather(se1p_plan *p, int n, const void *grid, double *phi, double *frc,
-                                         int add_self, cudaStream_t s);
+                                         int flags, cudaStream_t s);
+void launch_vjp_combine(int n, const double *q, const double *v, const double *Eq, const double *phiv,
+                        const double *Ev, double *grad_x, double *grad_q, cudaStream_t s);
 void launch_finalize(se1p_plan *p, int n, double *phi, double *frc, double *energy, cudaStream_t s);
 template <typename T> void launch_grid_to_double(se1p_plan *p, const void *src, double *dst, cudaStream_t s);
 template <typename T> void launch_grid_from_double(se1p_plan *p, const double *src, void *dst, cudaStream_t s);
@@ -92,7 +98,8 @@ template <typename T> int configure_fourier_kernels(se1p_plan *p);
 void launch_vico_table(se1p_plan *p, cudaStream_t s);
 
 // ---- se1p_real.cu
+// flags: bit 0 accumulates into phi/frc (else they are overwritten), bit 1 writes the field
 template <typename T> void launch_real_space(se1p_plan *p, int n, const int *cell_key, double *phi, double *frc,
-                                             int accumulate, cudaStream_t s);
+                                             int flags, cudaStream_t s);
 
 }  // namespace se1p

@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(32 * kRealWarps) k_real(Geo g, int n, const in
     if (valid) {
         // the kRealSplit warps of a target group combine through FP64 atomics
         // (outputs are zeroed beforehand when not accumulating)
-        const double qm = (double)me.q;
+        const double qm = (accumulate & 2) ? 1.0 : (double)me.q;  // bit 1: field instead of force
         const int o = me.orig;
         atomicAdd(phi + o, aphi);
         atomicAdd(frc + 3 * o, qm * afx);
@@ -266,7 +266,7 @@ void launch_real_space(se1p_plan *p, int n, const int *cell_key, double *phi, do
 {
     const Geo &g = p->geo;
     if (n <= 0) return;
-    if (!accumulate) {
+    if (!(accumulate & 1)) {
         cudaMemsetAsync(phi, 0, sizeof(double) * (size_t)n, s);
         cudaMemsetAsync(frc, 0, sizeof(double) * 3 * (size_t)n, s);
     }

@@ -125,7 +125,10 @@ def config_c3(n: int = 1_000_000) -> System:
 
 
 def config_c4(n: int = 200_000) -> System:
-    """N=200k in 8 Gaussian blobs (sigma=0.05) in L=[1,1,2], +-1."""
+    """N=200k in 8 Gaussian blobs (sigma=0.05) in L=[1,1,2], +-1.
+
+    The lowest z mode is k3 = pi (L3 = 2), so the I slabs use s_l = 4 (nI = 384):
+    the quadrature error of Section 4.2 behaves like exp(-|k3| s_l Lt)."""
     x, q = clustered(n, seed=3)
     return System(x, q, (1.0, 1.0, 2.0), dict(xi=20.0, M=(64, 64, 128), P=24, Mt=96, n0=288,
-                                                nI=192, nl=4, rc=0.15), "C4")
+                                                nI=384, nl=4, rc=0.15), "C4")

@@ -29,6 +29,7 @@ STATUS = {
 # every symbol include/se1p.h declares
 EXPORTS = (
     "se1p_plan_create", "se1p_plan_destroy", "se1p_plan_get_info", "se1p_eval", "se1p_eval_host",
+    "se1p_eval_vjp",
     "se1p_spread", "se1p_fourier", "se1p_gather", "se1p_real_space", "se1p_plan_set_profiling",
     "se1p_plan_stage_times", "se1p_plan_sync_status", "se1p_real_space_noalloc", "se1p_status_string",
 )
@@ -79,6 +80,7 @@ def load(path: str | None = None):
     lib.se1p_plan_get_info.argtypes = [vp, ctypes.POINTER(se1p_plan_info)]
     lib.se1p_eval.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
     lib.se1p_eval_host.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
+    lib.se1p_eval_vjp.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
     lib.se1p_spread.argtypes = [vp, i, vp, vp, vp, vp]
     lib.se1p_fourier.argtypes = [vp, vp, vp, vp]
     lib.se1p_gather.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
@@ -162,6 +164,11 @@ def se1p_eval(plan, n, x, q, phi=None, force=None, energy=None, stream=None) -> 
 def se1p_eval_host(plan, n, x, q, phi=None, force=None, energy=None, stream=None) -> None:
     _check(load().se1p_eval_host(plan, int(n), _ptr(x), _ptr(q), _ptr(phi), _ptr(force), _ptr(energy),
                                  _stream(stream)), "se1p_eval_host")
+
+
+def se1p_eval_vjp(plan, n, x, q, v_phi, grad_x=None, grad_q=None, stream=None) -> None:
+    _check(load().se1p_eval_vjp(plan, int(n), _ptr(x), _ptr(q), _ptr(v_phi), _ptr(grad_x), _ptr(grad_q),
+                                _stream(stream)), "se1p_eval_vjp")
 
 
 def se1p_spread(plan, n, x, q, grid, stream=None) -> None:

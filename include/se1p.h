@@ -190,6 +190,47 @@ se1p_status se1p_plan_stage_times(se1p_plan *plan, double *ms, int *n_evals);
  * error recorded since the last call), then clear it. */
 se1p_status se1p_plan_sync_status(se1p_plan *plan, void *stream);
 
+/* ---- parameter selection (Section 4.3) ---- */
+
+typedef struct {
+    double L[3];   /* box; L[0] == L[1]                                       */
+    double xi;     /* Ewald splitting parameter                              */
+    double Q;      /* sum of q^2 of the system                               */
+    int n;         /* number of particles                                    */
+    double tol;    /* requested rms error (absolute, per Eqs. 2.7-2.8, 4.3)  */
+    int precision; /* copied into the result                                 */
+} se1p_tune_request;
+
+/* Choose every field of *out for a requested tolerance, following Section 4.3:
+ *   rc from Eq. 2.9 and k_inf from Eq. 2.10 (Lambert W), M = 2 k_inf per axis
+ *   (scaled by the axis length; even 2^a 3^b 5^c 7^d sizes), P from Eq. 4.3 (even,
+ *   at most 32); k_inf and P are taken for tol/100 (the printed estimates undershoot
+ *   the measured k-space error by 5-20x), s_l from exp(-|k3| s_l L) <= tol at the lowest mode k3 = 2 pi/L3
+ *   (Section 4.2; Eq. 4.8 when L3 = L), n_l = ceil(M/10) (Eq. 4.9), s0 = 2 sqrt 2;
+ *   Mt, n0, nI are then fixed to smooth sizes.  Host only, no GPU work.
+ *   SE1P_ERR_INVALID_ARG for non-positive lengths, xi, Q, n or tol outside (0,1). */
+se1p_status se1p_autotune(const se1p_tune_request *req, se1p_params *out);
+
+/* ---- batched evaluation (many independent systems) ----
+ *
+ * A batch owns one plan per system (params[i], n_max[i]).  se1p_batch_eval
+ * evaluates all systems from packed arrays: system i occupies particles
+ * offsets[i] .. offsets[i+1]-1 (host array of count+1 ints) of x [*][3], q, phi,
+ * force; energy[i] receives its U.  The work of all systems is captured once
+ * into a CUDA graph (nodes spread over up to 8 streams, so small systems run
+ * concurrently) and replayed with one graph launch per call; the graph is
+ * re-captured when the sizes or the pointers change.  Device pointers;
+ * asynchronous on `stream`.  se1p_batch_sync_status synchronises and returns
+ * the first device status of any system (then clears them). */
+typedef struct se1p_batch se1p_batch;
+se1p_status se1p_batch_create(int count, const se1p_params *params, const int *n_max, se1p_batch **batch);
+se1p_status se1p_batch_destroy(se1p_batch *batch);
+se1p_status se1p_batch_eval(se1p_batch *batch, const int *offsets, const double *x, const double *q,
+                            double *phi, double *force, double *energy, void *stream);
+se1p_status se1p_batch_sync_status(se1p_batch *batch, void *stream);
+/* The plan of system i (owned by the batch), e.g. for se1p_plan_get_info; NULL if out of range. */
+se1p_plan *se1p_batch_plan(se1p_batch *batch, int i);
+
 /* ---- allocation-free variant ----
  *
  * se1p_real_space_noalloc: the real-space part (phi^R and F^R, as

@@ -1,0 +1,283 @@
+// Parameter selection (Section 4.3) and batched evaluation of many systems.
+//
+// se1p_autotune follows the paper's recipe for a requested rms tolerance:
+//   rc   from the real-space truncation estimate inverted with Lambert W (Eq. 2.9)
+//   M    = 2 k_inf per axis, k_inf from the k-space estimate inverted with Lambert W
+//        (Eq. 2.10) at tol/100, scaled by each axis' length, even smooth sizes
+//   P    from A exp(-c^2 pi P / 2) <= tol/100 (Eq. 4.3), A = sqrt(Q xi L)/L, even, <= 32
+//   s_l  from the quadrature estimate exp(-|k3| s Lt) <= tol at the lowest z mode
+//        k3 = 2 pi / L3 (Section 4.2; Eq. 4.8 is the case L3 = L), with L for Lt
+//   n_l  ~ M / 10 (Eq. 4.9), s0 = 2 sqrt 2; Mt, n0, nI smooth sizes.
+// se1p_batch_* evaluate many independent systems (own plans) from one captured
+// CUDA graph whose nodes are spread over several streams.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "se1p_plan.h"
+
+namespace {
+
+constexpr double kPiT = 3.14159265358979323846;
+constexpr double kC = 0.95;
+// Inverting the k-space estimates (Eqs. 2.8/2.10 and 4.3) at the requested tolerance
+// lands the measured k-space rms error 5-20x above it on uniform test systems
+// (checked against the direct sums); k_inf and P are therefore chosen for tol/100.
+// The real-space estimate (Eqs. 2.7/2.9) is used as printed.
+constexpr double kKspaceSafety = 100.0;
+
+// Principal branch of Lambert W for x >= 0 (w e^w = x), Halley's iteration.
+double lambert_w(double x)
+{
+    if (x <= 0.0) return 0.0;
+    double w = x < 1.0 ? x * (1.0 - x) : log(x) - log(log(x) + 1.0);
+    if (w < 0.0) w = 0.0;
+    for (int it = 0; it < 60; ++it) {
+        const double e = exp(w);
+        const double f = w * e - x;
+        const double d = e * (w + 1.0) - (w + 2.0) * f / (2.0 * w + 2.0);
+        const double dw = f / d;
+        w -= dw;
+        if (fabs(dw) <= 1e-15 * (1.0 + fabs(w))) break;
+    }
+    return w;
+}
+
+bool smooth(long n)
+{
+    if (n < 1) return false;
+    for (int p : {2, 3, 5, 7})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+int next_smooth_even(long n)
+{
+    if (n < 2) n = 2;
+    if (n & 1) ++n;
+    while (!smooth(n)) n += 2;
+    return (int)n;
+}
+
+int next_smooth_any(long n)
+{
+    if (n < 1) n = 1;
+    while (!smooth(n)) ++n;
+    return (int)n;
+}
+
+}  // namespace
+
+struct se1p_batch {
+    std::vector<se1p_plan *> plans;
+    std::vector<int> n_max;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
+    cudaStream_t capture = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // key of the captured graph
+    std::vector<int> key_n;
+    const void *key_ptr[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+extern "C" {
+
+se1p_status se1p_autotune(const se1p_tune_request *req, se1p_params *out)
+{
+    if (!req || !out) return SE1P_ERR_INVALID_ARG;
+    for (int i = 0; i < 3; ++i)
+        if (!(req->L[i] > 0.0) || !isfinite(req->L[i])) return SE1P_ERR_INVALID_ARG;
+    if (req->L[0] != req->L[1] || !(req->xi > 0.0) || !(req->tol > 0.0) || !(req->tol < 1.0) ||
+        !(req->Q > 0.0) || req->n < 1)
+        return SE1P_ERR_INVALID_ARG;
+    const double xi = req->xi, eps = req->tol, Q = req->Q;
+    const double V = req->L[0] * req->L[1] * req->L[2];
+    const double Lc = cbrt(V);  // cube of equal volume stands in for L^3 in Eqs. 2.9-2.10
+    se1p_params p;
+    memset(&p, 0, sizeof(p));
+    for (int i = 0; i < 3; ++i) p.L[i] = req->L[i];
+    p.xi = xi;
+    // Eq. 2.9: rc = (1/2xi) [3 W(4/3 C^{2/3})]^{1/2}, C = Q / (2 L^3 xi eps^2)
+    const double C = Q / (2.0 * V * xi * eps * eps);
+    double rc = 0.5 / xi * sqrt(3.0 * lambert_w(4.0 / 3.0 * pow(C, 2.0 / 3.0)));
+    if (rc > req->L[2]) rc = req->L[2];
+    p.rc = rc;
+    // Eq. 2.10: k_inf = (sqrt3 L xi / 2 pi) [W(D / (xi eps^2)^{2/3})]^{1/2}, D = 4/(3 L^2) (Q/pi)^{2/3}
+    const double epk = eps / kKspaceSafety;
+    const double D = 4.0 / (3.0 * Lc * Lc) * pow(Q / kPiT, 2.0 / 3.0);
+    const double wk = sqrt(lambert_w(D / pow(xi * epk * epk, 2.0 / 3.0)));
+    int M[3];
+    for (int i = 0; i < 3; ++i) {
+        const double kinf = sqrt(3.0) * req->L[i] * xi / (2.0 * kPiT) * wk;
+        M[i] = next_smooth_even((long)ceil(2.0 * kinf));
+    }
+    M[1] = M[0];
+    // Eq. 4.3: A exp(-c^2 pi P / 2) <= eps, A = sqrt(Q xi L) / L
+    const double A = sqrt(Q * xi * Lc) / Lc;
+    int P = (int)ceil(2.0 * log(fmax(A / epk, 1.0)) / (kC * kC * kPiT));
+    if (P & 1) ++P;
+    if (P < 4) P = 4;
+    if (P > 32) P = 32;
+    if (P > M[0]) P = M[0] & ~1;
+    if (P > M[2]) {
+        M[2] = next_smooth_even(P);
+    }
+    p.M[0] = M[0];
+    p.M[1] = M[1];
+    p.M[2] = M[2];
+    p.P = P;
+    const double h = req->L[0] / M[0];
+    p.Mt = next_smooth_any(M[0] + P);
+    p.n0 = next_smooth_any((long)ceil(2.0 * sqrt(2.0) * p.Mt - 1e-9));
+    // Section 4.2: exp(-|k3| s L) <= eps at k3 = 2 pi / L3
+    const double k3min = 2.0 * kPiT / req->L[2];
+    double sl = log(1.0 / eps) / (k3min * req->L[0]);
+    if (sl < 1.0) sl = 1.0;
+    p.nI = next_smooth_any((long)ceil(sl * p.Mt - 1e-9));
+    // Eq. 4.9: M ~ 10 n_l (free-axis units)
+    p.nl = (int)ceil(M[0] / 10.0);
+    if (p.nl < 1) p.nl = 1;
+    p.s0 = (double)p.n0 / p.Mt;
+    p.sl = (double)p.nI / p.Mt;
+    p.tol = eps;
+    p.precision = req->precision;
+    (void)h;
+    *out = p;
+    return SE1P_OK;
+}
+
+se1p_status se1p_batch_create(int count, const se1p_params *params, const int *n_max, se1p_batch **out)
+{
+    if (!out) return SE1P_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (count < 1 || !params || !n_max) return SE1P_ERR_INVALID_ARG;
+    se1p_batch *b = new (std::nothrow) se1p_batch();
+    if (!b) return SE1P_ERR_ALLOC;
+    for (int i = 0; i < count; ++i) {
+        se1p_plan *pl = nullptr;
+        se1p_status st = se1p_plan_create(params + i, n_max[i], &pl);
+        if (st != SE1P_OK) {
+            se1p_batch_destroy(b);
+            return st;
+        }
+        b->plans.push_back(pl);
+        b->n_max.push_back(n_max[i]);
+    }
+    const int ns = count < 8 ? count : 8;
+    for (int k = 0; k < ns; ++k) {
+        cudaStream_t s;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            se1p_batch_destroy(b);
+            return SE1P_ERR_CUDA;
+        }
+        b->streams.push_back(s);
+    }
+    for (int k = 0; k < 2 * ns + 1; ++k) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            se1p_batch_destroy(b);
+            return SE1P_ERR_CUDA;
+        }
+        b->events.push_back(e);
+    }
+    if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess) {
+        se1p_batch_destroy(b);
+        return SE1P_ERR_CUDA;
+    }
+    *out = b;
+    return SE1P_OK;
+}
+
+se1p_status se1p_batch_destroy(se1p_batch *b)
+{
+    if (!b) return SE1P_OK;
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+    for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+    if (b->capture) cudaStreamDestroy(b->capture);
+    for (se1p_plan *p : b->plans) se1p_plan_destroy(p);
+    delete b;
+    return SE1P_OK;
+}
+
+se1p_status se1p_batch_eval(se1p_batch *b, const int *offsets, const double *x, const double *q, double *phi,
+                            double *force, double *energy, void *stream)
+{
+    if (!b || !offsets || !x || !q) return SE1P_ERR_INVALID_ARG;
+    const int count = (int)b->plans.size();
+    std::vector<int> n(count);
+    for (int i = 0; i < count; ++i) {
+        n[i] = offsets[i + 1] - offsets[i];
+        if (n[i] < 0 || n[i] > b->n_max[i]) return SE1P_ERR_INVALID_ARG;
+    }
+    const void *ptrs[5] = {x, q, phi, force, energy};
+    bool same = b->exec && b->key_n == n;
+    for (int k = 0; k < 5 && same; ++k) same = b->key_ptr[k] == ptrs[k];
+    if (!same) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+        cudaStream_t c = b->capture;
+        if (cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SE1P_ERR_CUDA;
+        const int ns = (int)b->streams.size();
+        // fork: every worker stream waits on the capture origin
+        cudaEventRecord(b->events[0], c);
+        for (int k = 0; k < ns; ++k) cudaStreamWaitEvent(b->streams[k], b->events[0], 0);
+        se1p_status st = SE1P_OK;
+        for (int i = 0; i < count && st == SE1P_OK; ++i) {
+            cudaStream_t s = b->streams[i % ns];
+            const int o = offsets[i];
+            st = se1p_eval(b->plans[i], n[i], x + 3 * (size_t)o, q + o, phi ? phi + o : nullptr,
+                           force ? force + 3 * (size_t)o : nullptr, energy ? energy + i : nullptr, s);
+        }
+        // join
+        for (int k = 0; k < ns; ++k) {
+            cudaEventRecord(b->events[1 + k], b->streams[k]);
+            cudaStreamWaitEvent(c, b->events[1 + k], 0);
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(c, &g);
+        if (st != SE1P_OK || ec != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return st != SE1P_OK ? st : SE1P_ERR_CUDA;
+        }
+        if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+            cudaGraphDestroy(g);
+            cudaGetLastError();
+            return SE1P_ERR_CUDA;
+        }
+        b->graph = g;
+        b->key_n = n;
+        for (int k = 0; k < 5; ++k) b->key_ptr[k] = ptrs[k];
+    }
+    if (cudaGraphLaunch(b->exec, (cudaStream_t)stream) != cudaSuccess) return SE1P_ERR_CUDA;
+    return SE1P_OK;
+}
+
+se1p_status se1p_batch_sync_status(se1p_batch *b, void *stream)
+{
+    if (!b) return SE1P_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return SE1P_ERR_CUDA;
+    se1p_status first = SE1P_OK;
+    for (se1p_plan *p : b->plans) {
+        const se1p_status st = se1p_plan_sync_status(p, nullptr);
+        if (first == SE1P_OK && st != SE1P_OK) first = st;
+    }
+    return first;
+}
+
+se1p_plan *se1p_batch_plan(se1p_batch *b, int i)
+{
+    if (!b || i < 0 || i >= (int)b->plans.size()) return nullptr;
+    return b->plans[i];
+}
+
+}  // extern "C"

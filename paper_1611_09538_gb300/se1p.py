@@ -32,6 +32,8 @@ EXPORTS = (
     "se1p_eval_vjp",
     "se1p_spread", "se1p_fourier", "se1p_gather", "se1p_real_space", "se1p_plan_set_profiling",
     "se1p_plan_stage_times", "se1p_plan_sync_status", "se1p_real_space_noalloc", "se1p_status_string",
+    "se1p_autotune", "se1p_batch_create", "se1p_batch_destroy", "se1p_batch_eval", "se1p_batch_sync_status",
+    "se1p_batch_plan",
 )
 
 STAGES = ("pack", "spread", "fourier", "gather", "real", "final")
@@ -58,6 +60,13 @@ class se1p_plan_info(ctypes.Structure):
         ("nl", ctypes.c_int), ("n_I_modes", ctypes.c_int), ("P", ctypes.c_int), ("precision", ctypes.c_int),
         ("h", ctypes.c_double), ("hz", ctypes.c_double), ("eta", ctypes.c_double), ("etaz", ctypes.c_double),
         ("R", ctypes.c_double), ("cells", ctypes.c_int * 3), ("workspace_bytes", ctypes.c_size_t),
+    ]
+
+
+class se1p_tune_request(ctypes.Structure):
+    _fields_ = [
+        ("L", ctypes.c_double * 3), ("xi", ctypes.c_double), ("Q", ctypes.c_double), ("n", ctypes.c_int),
+        ("tol", ctypes.c_double), ("precision", ctypes.c_int),
     ]
 
 
@@ -91,8 +100,15 @@ def load(path: str | None = None):
     lib.se1p_real_space_noalloc.argtypes = [ctypes.POINTER(se1p_params), i, vp, vp, vp, vp, vp]
     lib.se1p_status_string.argtypes = [i]
     lib.se1p_status_string.restype = ctypes.c_char_p
+    lib.se1p_autotune.argtypes = [ctypes.POINTER(se1p_tune_request), ctypes.POINTER(se1p_params)]
+    lib.se1p_batch_create.argtypes = [i, ctypes.POINTER(se1p_params), ctypes.POINTER(i), ctypes.POINTER(vp)]
+    lib.se1p_batch_destroy.argtypes = [vp]
+    lib.se1p_batch_eval.argtypes = [vp, ctypes.POINTER(i), vp, vp, vp, vp, vp, vp]
+    lib.se1p_batch_sync_status.argtypes = [vp, vp]
+    lib.se1p_batch_plan.argtypes = [vp, i]
+    lib.se1p_batch_plan.restype = vp
     for name in EXPORTS:
-        if name != "se1p_status_string":
+        if name not in ("se1p_status_string", "se1p_batch_plan"):
             getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -215,6 +231,42 @@ def se1p_real_space_noalloc(params: se1p_params, n, x, q, phi, force, stream=Non
 
 def se1p_status_string(code: int) -> str:
     return load().se1p_status_string(int(code)).decode()
+
+
+def se1p_autotune(L, xi, Q, n, tol, precision=SE1P_FP64) -> se1p_params:
+    req = se1p_tune_request()
+    req.L[:] = [float(v) for v in L]
+    req.xi, req.Q, req.n, req.tol, req.precision = float(xi), float(Q), int(n), float(tol), int(precision)
+    out = se1p_params()
+    _check(load().se1p_autotune(ctypes.byref(req), ctypes.byref(out)), "se1p_autotune")
+    return out
+
+
+def se1p_batch_create(params_list, n_max_list) -> int:
+    count = len(params_list)
+    arr = (se1p_params * count)(*params_list)
+    nm = (ctypes.c_int * count)(*[int(v) for v in n_max_list])
+    h = ctypes.c_void_p()
+    _check(load().se1p_batch_create(count, arr, nm, ctypes.byref(h)), "se1p_batch_create")
+    return h.value
+
+
+def se1p_batch_destroy(batch) -> None:
+    _check(load().se1p_batch_destroy(batch), "se1p_batch_destroy")
+
+
+def se1p_batch_eval(batch, offsets, x, q, phi=None, force=None, energy=None, stream=None) -> None:
+    off = (ctypes.c_int * len(offsets))(*[int(v) for v in offsets])
+    _check(load().se1p_batch_eval(batch, off, _ptr(x), _ptr(q), _ptr(phi), _ptr(force), _ptr(energy),
+                                  _stream(stream)), "se1p_batch_eval")
+
+
+def se1p_batch_sync_status(batch, stream=None) -> int:
+    return int(load().se1p_batch_sync_status(batch, _stream(stream)))
+
+
+def se1p_batch_plan(batch, i: int) -> int:
+    return load().se1p_batch_plan(batch, int(i))
 
 
 # ------------------------------------------------------------------ convenience wrapper

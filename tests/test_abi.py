@@ -22,7 +22,7 @@ def lib():
 def declared_symbols():
     with open(os.path.join(ROOT, "include", "se1p.h")) as f:
         text = f.read()
-    return sorted(set(re.findall(r"^\s*(?:se1p_status|const char \*)\s*(se1p_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:se1p_status|const char \*|se1p_plan \*)\s*(se1p_\w+)\s*\(", text, re.M)))
 
 
 def test_header_and_binding_agree():

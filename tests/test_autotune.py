@@ -1,0 +1,67 @@
+"""Parameter selection (Section 4.3) through the C ABI's host-only se1p_autotune.
+
+Checked against the oracles: on a Table 4.1-like system (N=120, L=10, Q=1) the
+chosen parameters must reach the requested tolerance in the k-space potential
+(numpy restatement of Algorithm 1 vs the direct sums) and in the real-space
+truncation (direct sums at rc vs converged rc)."""
+import numpy as np
+import pytest
+
+from oracle import direct
+from oracle import se1p_algorithm as se
+from paper_1611_09538_gb300 import build as se1p_build
+from paper_1611_09538_gb300 import se1p
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    se1p_build.build()
+    se1p.load()
+
+
+def _system():
+    rng = np.random.default_rng(41)
+    n, L = 120, 10.0
+    x = rng.random((n, 3)) * L
+    q = np.where(np.arange(n) % 2 == 0, 1.0, -1.0) / np.sqrt(n)
+    return x, q, L
+
+
+@pytest.mark.parametrize("xi,tol", [(1.5, 1e-6), (3.0, 1e-6), (1.5, 1e-9), (3.0, 1e-9)])
+def test_autotuned_parameters_reach_tolerance(direct_oracle, xi, tol):
+    x, q, L = _system()
+    p = se1p.se1p_autotune((L, L, L), xi, float(np.sum(q * q)), len(q), tol)
+    assert p.M[0] % 2 == 0 and p.P % 2 == 0 and p.P <= 32 and p.Mt >= p.M[0] + p.P
+    assert p.n0 >= 2.4 * p.Mt and p.nI >= p.Mt and p.nl >= 1
+    pp, _ = direct.ewald1p_parts(x, q, L, xi, -1.0)
+    phi, _ = se.se1p_fourier(x, q, (L, L, L), xi, tuple(p.M), p.P, p.Mt, p.n0, p.nI, p.nl)
+    assert np.sqrt(np.mean((phi - (pp[:, 1] + pp[:, 2])) ** 2)) < tol
+    pr, _ = direct.ewald1p_parts(x, q, L, xi, p.rc)
+    pc, _ = direct.ewald1p_parts(x, q, L, xi, 6.5 / xi)
+    assert np.sqrt(np.mean((pr[:, 0] - pc[:, 0]) ** 2)) < 2.5 * tol
+
+
+def test_table_4_1_grid_sizes_at_moderate_accuracy():
+    """Table 4.1 rows 1-2 (tol 1e-6): M = 32 and 64, P = 12 within one step of 2."""
+    for xi, M, P in ((1.5, 32, 12), (3.0, 64, 12)):
+        p = se1p.se1p_autotune((10.0, 10.0, 10.0), xi, 1.0, 120, 1e-6)
+        assert abs(p.M[0] - M) <= 0.15 * M
+        assert abs(p.P - P) <= 2
+
+
+def test_elongated_box_upsamples_low_modes():
+    """The lowest z mode of a long box (k3 = 2 pi / L3) needs s_l ~ ln(1/tol) L3 / (2 pi L)."""
+    p1 = se1p.se1p_autotune((1.0, 1.0, 1.0), 20.0, 1e4, 10000, 1e-6)
+    p4 = se1p.se1p_autotune((1.0, 1.0, 4.0), 20.0, 1e4, 10000, 1e-6)
+    assert p4.sl > 3.5 * p1.sl
+    assert p4.M[2] > 3.5 * p1.M[2] and p4.M[0] == p1.M[0]
+
+
+@pytest.mark.parametrize("bad", [
+    dict(L=(1, 2, 1)), dict(xi=0.0), dict(tol=0.0), dict(tol=1.0), dict(Q=0.0), dict(n=0)])
+def test_autotune_rejects_bad_requests(bad):
+    kw = dict(L=(1.0, 1.0, 1.0), xi=8.0, Q=10.0, n=100, tol=1e-6)
+    kw.update(bad)
+    with pytest.raises(se1p.SE1PError) as ei:
+        se1p.se1p_autotune(kw["L"], kw["xi"], kw["Q"], kw["n"], kw["tol"])
+    assert ei.value.code == 1

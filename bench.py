@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64-throughput and batched-workload side measurements")
     ap.add_argument("--profile-only", action="store_true",
                     help="only warm-up + timed steps (for ncu launch lists); prints a short line")
     return ap.parse_args()
@@ -377,6 +379,9 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clocks,
         "accuracy": acc,
     }
+    if not args.no_extras:
+        out["fp64"] = measure_fp64(sys_, p, n, x, q, stream, min(args.steps, 20))
+        out["batched"] = measure_batched(stream)
     if not args.no_cpu_baseline and world == 1:
         cb = oracle_sample(sys_, args.cpu_seconds)
         t = cb["targets"]
@@ -390,6 +395,64 @@ def run_gpu(args, rank, world, local_rank):
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def measure_fp64(sys_, p, n, x, q, stream, steps):
+    """Throughput of the plain FP64 form on the same workload (inputs resident)."""
+    import torch
+    from paper_1611_09538_gb300 import se1p
+    plan = se1p.Plan(sys_.L, p["xi"], p["M"], p["P"], n, Mt=p["Mt"], n0=p["n0"], nI=p["nI"], nl=p["nl"],
+                     rc=p["rc"], precision=se1p.SE1P_FP64)
+    phi = torch.empty(n, dtype=torch.float64, device="cuda")
+    F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    E = torch.empty(1, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        se1p.se1p_eval(plan.handle, n, x, q, phi, F, E, stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(steps):
+        se1p.se1p_eval(plan.handle, n, x, q, phi, F, E, stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    plan.close()
+    return {"value": n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps}
+
+
+def measure_batched(stream, steps=5):
+    """64 independent neutral systems (N log-uniform in [1k, 50k], L = [1,1,Lz], Lz in [1,4],
+    xi = 20, parameters from se1p_autotune at rms 1e-6, mixed precision), one graph launch
+    per step."""
+    import torch
+    from paper_1611_09538_gb300 import inputs, se1p
+    systems = inputs.batch_systems(count=64, n_lo=1000, n_hi=50000, seed=4)
+    params = [se1p.se1p_autotune(s.L, 20.0, float(np.sum(s.q ** 2)), len(s.q), 1e-6, se1p.SE1P_MIXED)
+              for s in systems]
+    offsets = np.concatenate([[0], np.cumsum([len(s.q) for s in systems])]).astype(int)
+    ntot = int(offsets[-1])
+    x = torch.as_tensor(np.concatenate([s.x for s in systems]), device="cuda").contiguous()
+    q = torch.as_tensor(np.concatenate([s.q for s in systems]), device="cuda").contiguous()
+    phi = torch.empty(ntot, dtype=torch.float64, device="cuda")
+    F = torch.empty((ntot, 3), dtype=torch.float64, device="cuda")
+    E = torch.empty(len(systems), dtype=torch.float64, device="cuda")
+    b = se1p.se1p_batch_create(params, [len(s.q) for s in systems])
+    for _ in range(2):
+        se1p.se1p_batch_eval(b, offsets, x, q, phi, F, E, stream)
+    st = se1p.se1p_batch_sync_status(b, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        se1p.se1p_batch_eval(b, offsets, x, q, phi, F, E, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    se1p.se1p_batch_destroy(b)
+    return {"value": ntot / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "systems": len(systems),
+            "particles": ntot, "status": se1p.STATUS.get(st), "precision": "mixed",
+            "workload": "64 systems, N log-uniform in [1k,50k], L=[1,1,Lz], Lz~U[1,4], xi=20, "
+                        "autotuned at rms 1e-6, one CUDA-graph launch per step"}
 
 
 # ------------------------------------------------------------------ reference arm (the oracle)

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "se1p_plan.h"
 
 namespace se1p {
@@ -359,8 +361,11 @@ __global__ void __launch_bounds__(256) k_gather(Geo g, int n, const PartRec<T> *
                                                 int flags)
 {
     // flags: bit 0 adds the self term (Eq. 2.5); bit 1 writes the field -grad phi
-    // instead of the force -q grad phi
-    __shared__ T sy[8][2][32], sz[8][2][32];
+    // instead of the force -q grad phi.
+    // Per warp: y window values interleaved as (wy_j, wy_j dy_j) so that one
+    // 16-byte shared load (float) serves two rows; z values (wz, wz dz) per row.
+    __shared__ __align__(16) T sy[8][34][2];
+    __shared__ T sz[8][2][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int P = PC > 0 ? PC : g.P;  // compile-time support width when PC > 0 (loops unroll)
     const int warps_total = gridDim.x * (blockDim.x >> 5);
@@ -374,10 +379,13 @@ __global__ void __launch_bounds__(256) k_gather(Geo g, int n, const PartRec<T> *
             wx = w[lane];
             wxd = wx * (r.g[0] - jc) * h;
             const T wy = w[P + lane], wz = w[2 * P + lane];
-            sy[wib][0][lane] = wy;
-            sy[wib][1][lane] = wy * (r.g[1] - jc) * h;
+            sy[wib][lane][0] = wy;
+            sy[wib][lane][1] = wy * (r.g[1] - jc) * h;
             sz[wib][0][lane] = wz;
             sz[wib][1][lane] = wz * (r.g[2] - jc) * hz;
+        } else if (lane < 34 - 0 && lane >= P && lane < 34) {
+            sy[wib][lane][0] = (T)0;  // pad for the paired loads of an odd P
+            sy[wib][lane][1] = (T)0;
         }
         __syncwarp();
         T aphi = 0, afy = 0, afz = 0;
@@ -387,11 +395,27 @@ __global__ void __launch_bounds__(256) k_gather(Geo g, int n, const PartRec<T> *
                 if (zk >= g.M3) zk -= g.M3;
                 const T *row = grid + ((size_t)zk * g.Mt + r.i0[1]) * g.Mt + r.i0[0] + lane;
                 T a = 0, b = 0;
-#pragma unroll(PC > 0 ? PC : 1)
-                for (int j = 0; j < P; ++j) {
-                    const T v = __ldg(row + (size_t)j * g.Mt);
-                    a += sy[wib][0][j] * v;
-                    b += sy[wib][1][j] * v;
+#pragma unroll(PC > 0 ? (PC + 1) / 2 : 1)
+                for (int j = 0; j < P; j += 2) {
+                    T wy0, wd0, wy1, wd1;
+                    if constexpr (sizeof(T) == 4) {
+                        const float4 ww = *reinterpret_cast<const float4 *>(&sy[wib][j][0]);
+                        wy0 = ww.x;
+                        wd0 = ww.y;
+                        wy1 = ww.z;
+                        wd1 = ww.w;
+                    } else {
+                        wy0 = sy[wib][j][0];
+                        wd0 = sy[wib][j][1];
+                        wy1 = sy[wib][j + 1][0];
+                        wd1 = sy[wib][j + 1][1];
+                    }
+                    const T v0 = __ldg(row + (size_t)j * g.Mt);
+                    const T v1 = j + 1 < P ? __ldg(row + (size_t)(j + 1) * g.Mt) : (T)0;
+                    a += wy0 * v0;
+                    b += wd0 * v0;
+                    a += wy1 * v1;
+                    b += wd1 * v1;
                 }
                 aphi += sz[wib][0][k] * a;
                 afy += sz[wib][0][k] * b;
@@ -402,6 +426,110 @@ __global__ void __launch_bounds__(256) k_gather(Geo g, int n, const PartRec<T> *
         T vfx = warp_sum(wxd * aphi);
         T vfy = warp_sum(wx * afy);
         T vfz = warp_sum(wx * afz);
+        if (lane == 0) {
+            const double h3 = g.h * g.h * g.hz;
+            const double qd = (double)r.q;
+            double ph = h3 * (double)vphi;
+            if (flags & 1) ph += -2.0 * g.xi / sqrt(kPi) * qd;
+            phi[r.orig] = ph;
+            const double cxy = 4.0 * g.xi * g.xi / g.eta, cz = 4.0 * g.xi * g.xi / g.etaz;
+            const double qf = (flags & 2) ? 1.0 : qd;
+            frc[3 * r.orig + 0] = qf * h3 * cxy * (double)vfx;
+            frc[3 * r.orig + 1] = qf * h3 * cxy * (double)vfy;
+            frc[3 * r.orig + 2] = qf * h3 * cz * (double)vfz;
+        }
+        __syncwarp();
+    }
+}
+
+template <typename VT> __device__ __forceinline__ VT make_zero();
+template <> __device__ __forceinline__ float4 make_zero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+template <> __device__ __forceinline__ double2 make_zero<double2>() { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ float dotv(const float *w, float4 v) { return w[0] * v.x + w[1] * v.y + w[2] * v.z + w[3] * v.w; }
+__device__ __forceinline__ double dotv(const double *w, double2 v) { return w[0] * v.x + w[1] * v.y; }
+
+// Vectorised gathering for Mt a multiple of V = 16 / sizeof(T) (every grid row then
+// starts 16-byte aligned).  The x window [i0, i0+P) is covered from the aligned
+// start i0 & ~(V-1) by NQ = ceil((P + V - 1) / V) vectors; a warp instruction
+// loads RPR = 32 / NQ rows at once (lane = row-in-group x vector), so one request
+// brings 4 rows (FP32, P = 24) instead of one.  Each lane holds the x window
+// values of its V points (zero outside the support) and accumulates, per row,
+// sum wx H and sum wx dx H, weighted by the row's y values (wy, wy dy).
+template <typename T, int PC>
+__global__ void __launch_bounds__(256) k_gather_vec(Geo g, int n, const PartRec<T> *__restrict__ parts,
+                                                    const T *__restrict__ wts, const T *__restrict__ grid,
+                                                    double *__restrict__ phi, double *__restrict__ frc,
+                                                    int flags)
+{
+    constexpr int V = 16 / sizeof(T);
+    constexpr int NQ = (PC + V - 1 + V - 1) / V;
+    constexpr int RPR = 32 / NQ;                       // rows per warp request
+    constexpr int NJ = (PC + RPR - 1) / RPR * RPR;     // y rows padded to a multiple of RPR
+    using VecT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    __shared__ T sy[8][2][NJ];
+    __shared__ T sz[8][2][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int rr = lane / NQ, qv = lane - rr * NQ;  // row within the request, vector index
+    const bool active = rr < RPR;
+    const int warps_total = gridDim.x * (blockDim.x >> 5);
+    const T h = (T)g.h, hz = (T)g.hz;
+    for (int pi = blockIdx.x * (blockDim.x >> 5) + wib; pi < n; pi += warps_total) {
+        const PartRec<T> r = parts[pi];
+        const T *w = wts + (size_t)pi * 3 * PC;
+        for (int j = lane; j < NJ; j += 32) {
+            T wy = 0, wyd = 0;
+            if (j < PC) {
+                wy = w[PC + j];
+                wyd = wy * (r.g[1] - (T)(j - g.c)) * h;
+            }
+            sy[wib][0][j] = wy;
+            sy[wib][1][j] = wyd;
+        }
+        if (lane < PC) {
+            const T wz = w[2 * PC + lane];
+            sz[wib][0][lane] = wz;
+            sz[wib][1][lane] = wz * (r.g[2] - (T)(lane - g.c)) * hz;
+        }
+        // this lane's V x points: window index rel = base + V qv + e - i0
+        const int base = r.i0[0] & ~(V - 1);
+        T wx[V], wxd[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const int rel = base + V * qv + e - r.i0[0];
+            const bool in = active && rel >= 0 && rel < PC;
+            wx[e] = in ? w[rel] : (T)0;
+            wxd[e] = in ? wx[e] * (r.g[0] - (T)(rel - g.c)) * h : (T)0;
+        }
+        // only vectors holding at least one window point are read: such a vector starts at a
+        // multiple of V below i0 + P <= Mt and so ends inside the row (Mt % V == 0)
+        const bool ld = active && (base + V * qv < r.i0[0] + PC);
+        __syncwarp();
+        T aphi = 0, afx = 0, afy = 0, afz = 0;
+        if (ld) {
+            for (int k = 0; k < PC; ++k) {
+                int zk = r.i0[2] + k;
+                if (zk >= g.M3) zk -= g.M3;
+                const T *rowbase = grid + ((size_t)zk * g.Mt + r.i0[1]) * g.Mt + base + V * qv;
+                T a = 0, b = 0, c = 0;
+#pragma unroll
+                for (int j0 = 0; j0 < NJ; j0 += RPR) {
+                    const int j = j0 + rr;
+                    const T wy = sy[wib][0][j], wyd = sy[wib][1][j];
+                    VecT v = make_zero<VecT>();
+                    if (j < PC) v = *reinterpret_cast<const VecT *>(rowbase + (size_t)j * g.Mt);
+                    const T s1 = dotv(wx, v), s2 = dotv(wxd, v);
+                    a += wy * s1;
+                    b += wy * s2;
+                    c += wyd * s1;
+                }
+                const T wz = sz[wib][0][k], wzd = sz[wib][1][k];
+                aphi += wz * a;
+                afx += wz * b;
+                afy += wz * c;
+                afz += wzd * a;
+            }
+        }
+        const T vphi = warp_sum(aphi), vfx = warp_sum(afx), vfy = warp_sum(afy), vfz = warp_sum(afz);
         if (lane == 0) {
             const double h3 = g.h * g.h * g.hz;
             const double qd = (double)r.q;
@@ -538,7 +666,11 @@ void launch_gather(se1p_plan *p, int n, const void *grid, double *phi, double *f
     const T *w = (const T *)p->b.wts;
     const T *gr = (const T *)grid;
     const int nt = 32 * warps_per_block;
-    if (g.P == 24) k_gather<T, 24><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags);
+    constexpr int V = 16 / sizeof(T);
+    const bool vec = g.Mt % V == 0;
+    if (vec && g.P == 24) k_gather_vec<T, 24><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags);
+    else if (vec && g.P == 16) k_gather_vec<T, 16><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags);
+    else if (g.P == 24) k_gather<T, 24><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags);
     else if (g.P == 16) k_gather<T, 16><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags);
     else k_gather<T, 0><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags);
 }

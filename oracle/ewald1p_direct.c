@@ -205,16 +205,32 @@ int orc_ewald1p(int n, const double *x, const double *q, int nt, const int *tgt,
         if (exp(-a) / a < kcut) break;
         jmax = j;
     }
-    /* z images that can lie within rc (A15: all alpha with |alpha L3| <= rc + L3) */
+    /* z images that can lie within rc: all alpha with |alpha L3| <= rc + L3 */
     int amax = rc > 0.0 ? (int)ceil(rc / L3) + 1 : 0;
 
+    /* Work items are (target, source chunk) pairs so that a few targets still keep
+     * every thread busy; each item writes its partial sums, which are then added
+     * in a fixed order (the result does not depend on the thread count). */
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+#endif
+    int nchunk = 1;
+    if (nt > 0 && nt < 4 * nthr) nchunk = (4 * nthr + nt - 1) / nt;
+    if (nchunk > n) nchunk = n > 0 ? n : 1;
+    const int chunk = n > 0 ? (n + nchunk - 1) / nchunk : 0;
+    double *part = (double *)calloc((size_t)nt * nchunk * 12, sizeof(double));
+    if (!part && nt > 0) return -1;
+
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int it = 0; it < nt; ++it) {
+    for (long item = 0; item < (long)nt * nchunk; ++item) {
+        const int it = (int)(item / nchunk), ic = (int)(item % nchunk);
         const int m = tgt ? tgt[it] : it;
+        const int n0 = ic * chunk, n1 = n0 + chunk < n ? n0 + chunk : n;
         const double xm = x[3 * m], ym = x[3 * m + 1], zm = x[3 * m + 2];
         double pR = 0, pK = 0, p0 = 0;
         double fR[3] = {0, 0, 0}, fK[3] = {0, 0, 0}, f0[3] = {0, 0, 0};
-        for (int nn = 0; nn < n; ++nn) {
+        for (int nn = n0; nn < n1; ++nn) {
             const double qn = q[nn];
             const double dx = xm - x[3 * nn], dy = ym - x[3 * nn + 1], dz = zm - x[3 * nn + 2];
             const double rho2 = dx * dx + dy * dy;
@@ -259,17 +275,33 @@ int orc_ewald1p(int n, const double *x, const double *q, int nt, const int *tgt,
                 }
             }
         }
-        const double qm = q[m];
-        phi_out[4 * it + 0] = pR;
-        phi_out[4 * it + 1] = 2.0 / L3 * pK;
-        phi_out[4 * it + 2] = -1.0 / L3 * p0;
-        phi_out[4 * it + 3] = -two_xi_sqpi * qm;
+        double *o = part + ((size_t)it * nchunk + ic) * 12;
+        o[0] = pR;
+        o[1] = pK;
+        o[2] = p0;
         for (int d = 0; d < 3; ++d) {
-            frc_out[9 * it + d] = qm * fR[d];
-            frc_out[9 * it + 3 + d] = qm * 2.0 / L3 * fK[d];
-            frc_out[9 * it + 6 + d] = qm * 2.0 / L3 * f0[d];
+            o[3 + d] = fR[d];
+            o[6 + d] = fK[d];
+            o[9 + d] = f0[d];
         }
     }
+    for (int it = 0; it < nt; ++it) {
+        const int m = tgt ? tgt[it] : it;
+        double acc[12] = {0};
+        for (int ic = 0; ic < nchunk; ++ic)
+            for (int v = 0; v < 12; ++v) acc[v] += part[((size_t)it * nchunk + ic) * 12 + v];
+        const double qm = q[m];
+        phi_out[4 * it + 0] = acc[0];
+        phi_out[4 * it + 1] = 2.0 / L3 * acc[1];
+        phi_out[4 * it + 2] = -1.0 / L3 * acc[2];
+        phi_out[4 * it + 3] = -two_xi_sqpi * qm;
+        for (int d = 0; d < 3; ++d) {
+            frc_out[9 * it + d] = qm * acc[3 + d];
+            frc_out[9 * it + 3 + d] = qm * 2.0 / L3 * acc[6 + d];
+            frc_out[9 * it + 6 + d] = qm * 2.0 / L3 * acc[9 + d];
+        }
+    }
+    free(part);
     return 0;
 }
 

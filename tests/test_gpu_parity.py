@@ -72,6 +72,9 @@ CASES = {
                               nI=98, nl=2, rc=0.25),
     # C1-like: P = 16, M = 32, Mt = 48
     "c1_like": small_case(n=1000, seed=0, xi=8.0, M=(32, 32, 32), P=16, Mt=48, n0=144, nI=144, nl=3),
+    # elongated periodic axis: M3 = 256 (K3 = 129 z modes, 32 of them in the set I)
+    "elongated": small_case(n=600, L=(1.0, 1.0, 8.0), seed=6, xi=8.0, M=(32, 32, 256), P=16, Mt=48, n0=144,
+                            nI=96, nl=4, rc=0.3),
 }
 
 

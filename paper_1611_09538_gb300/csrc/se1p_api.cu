@@ -89,13 +89,18 @@ template <typename T> void upload(void *dst, const std::vector<T> &v)
     cudaMemcpy(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
-template <typename T> std::vector<Cx<T>> twiddles(int n)
+template <typename T> std::vector<Tw<T>> twiddles(int n)
 {
-    std::vector<Cx<T>> w(n);
+    std::vector<Tw<T>> w(n);
     for (int t = 0; t < n; ++t) {
         const double a = 2.0 * kPi * (double)t / (double)n;
-        w[t].re = (T)cos(a);
-        w[t].im = (T)(-sin(a));
+        const double c = cos(a), sn = -sin(a);
+        w[t].re = (T)c;
+        w[t].im = (T)sn;
+        if constexpr (sizeof(T) == sizeof(float)) {
+            w[t].lre = (float)(c - (double)w[t].re);
+            w[t].lim = (float)(sn - (double)w[t].im);
+        }
     }
     return w;
 }
@@ -106,38 +111,22 @@ template <typename T> se1p_status build_tables(se1p_plan *p, Alloc &A)
 {
     const Geo &g = p->geo;
     // twiddles
-    p->b.tw_z = A.dev(csize<T>() * p->M3);
+    p->b.tw_z = A.dev(sizeof(Tw<T>) * p->M3);
     for (int c = 0; c < 3; ++c) {
         SlabClass &C = p->cls[c];
         if (C.count == 0) continue;
-        C.tw = A.dev((c == 0 ? csize<double>() : csize<T>()) * C.ns);
+        C.tw = A.dev((c == 0 ? sizeof(Tw<double>) : sizeof(Tw<T>)) * C.ns);
         C.rows = A.dev((c == 0 ? csize<double>() : csize<T>()) * (size_t)C.count * p->Mt * C.ns);
-        if (c > 0) C.ex = A.dev(sizeof(T) * C.ns);
+        if (c > 0) C.sym = A.dev(sizeof(T) * (size_t)C.count * C.ns * C.ns);
     }
-    p->b.ez = A.dev(sizeof(T) * p->K3);
     if (!A.ok) return SE1P_ERR_ALLOC;
     upload(p->b.tw_z, twiddles<T>(p->M3));
     for (int c = 0; c < 3; ++c) {
         SlabClass &C = p->cls[c];
         if (C.count == 0) continue;
         if (c == 0) upload(C.tw, twiddles<double>(C.ns));
-        else {
-            upload(C.tw, twiddles<T>(C.ns));
-            std::vector<T> ex(C.ns);
-            const double dk = 2.0 * kPi / (C.ns * g.h);
-            for (int i = 0; i < C.ns; ++i) {
-                const double k = dk * signed_idx(i, C.ns);
-                ex[i] = (T)exp(-(1.0 - g.eta) * k * k / (4.0 * g.xi * g.xi));
-            }
-            upload(C.ex, ex);
-        }
+        else upload(C.tw, twiddles<T>(C.ns));
     }
-    std::vector<T> ez(p->K3);
-    for (int k = 0; k < p->K3; ++k) {
-        const double k3 = 2.0 * kPi * k / g.L[2];
-        ez[k] = (T)exp(-(1.0 - g.etaz) * k3 * k3 / (4.0 * g.xi * g.xi));
-    }
-    upload(p->b.ez, ez);
     return SE1P_OK;
 }
 
@@ -216,7 +205,7 @@ void run_pass(se1p_plan *p, int n, const double *x, const double *q, double *phi
     if (m) m->mark(SE1P_STAGE_FOURIER);
     launch_fourier<T>(p, s);
     if (m) m->mark(SE1P_STAGE_GATHER);
-    launch_gather<T>(p, n, p->b.grid, phi, frc, 1 | (field ? 2 : 0), s);
+    launch_gather<T>(p, n, p->b.grid, phi, frc, 1 | (field ? 2 : 0) | 4, s);
     if (m) m->mark(SE1P_STAGE_REAL);
     if (p->geo.rc > 0) launch_real_space<T>(p, n, p->b.cell_key, phi, frc, 1 | (field ? 2 : 0), s);
 }
@@ -262,6 +251,9 @@ se1p_status flags_to_status(int f)
 }
 
 bool bad_n(const se1p_plan *p, int n) { return n < 0 || n > p->n_max; }
+
+// The spread grid holds unnormalised windows; this factor turns it into Eq. 3.4's grid.
+double window_norm3(const se1p_plan *p) { return p->geo.wnorm_xy * p->geo.wnorm_xy * p->geo.wnorm_z; }
 
 }  // namespace
 
@@ -407,6 +399,8 @@ se1p_status se1p_plan_create(const se1p_params *prm, int n_max, se1p_plan **out)
     int cfg = mixed ? configure_fourier_kernels<float>(p) : configure_fourier_kernels<double>(p);
     if (cfg != 0) { cudaGetLastError(); free_all(p); delete p; return SE1P_ERR_CUDA; }
     launch_vico_table(p, 0);
+    if (mixed) launch_symbol_tables<float>(p, 0);
+    else launch_symbol_tables<double>(p, 0);
     if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) {
         free_all(p);
         delete p;
@@ -551,12 +545,12 @@ se1p_status se1p_spread(se1p_plan *p, int n, const double *x, const double *q, d
         launch_pack<float>(p, n, x, q, s);
         launch_sort_scatter<float>(p, n, s);
         launch_spread<float>(p, s);
-        launch_grid_to_double<float>(p, p->b.grid, grid, s);
+        launch_grid_to_double<float>(p, p->b.grid, grid, window_norm3(p), s);
     } else {
         launch_pack<double>(p, n, x, q, s);
         launch_sort_scatter<double>(p, n, s);
         launch_spread<double>(p, s);
-        launch_grid_to_double<double>(p, p->b.grid, grid, s);
+        launch_grid_to_double<double>(p, p->b.grid, grid, window_norm3(p), s);
     }
     return check_launch();
 }
@@ -568,11 +562,11 @@ se1p_status se1p_fourier(se1p_plan *p, const double *grid_in, double *grid_out, 
     if (p->precision == SE1P_MIXED) {
         launch_grid_from_double<float>(p, grid_in, p->b.grid, s);
         launch_fourier<float>(p, s);
-        launch_grid_to_double<float>(p, p->b.grid, grid_out, s);
+        launch_grid_to_double<float>(p, p->b.grid, grid_out, 1.0, s);
     } else {
         launch_grid_from_double<double>(p, grid_in, p->b.grid, s);
         launch_fourier<double>(p, s);
-        launch_grid_to_double<double>(p, p->b.grid, grid_out, s);
+        launch_grid_to_double<double>(p, p->b.grid, grid_out, 1.0, s);
     }
     return check_launch();
 }

@@ -23,7 +23,7 @@ __device__ __forceinline__ int signed_index(int i, int n) { return i <= (n - 1) 
 
 // ---- z forward: CTA = (y, chunk of xb x-values); smem [z][p]
 template <typename T>
-__global__ void k_zfwd(int M3, int Mt, int K3, FftDesc d, const Cx<T> *__restrict__ tw, int xb,
+__global__ void k_zfwd(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restrict__ tw, int xb,
                        const T *__restrict__ grid, Cx<T> *__restrict__ zspec, double *__restrict__ slab0)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -56,7 +56,7 @@ __global__ void k_zfwd(int M3, int Mt, int K3, FftDesc d, const Cx<T> *__restric
 
 // ---- x forward: CTA = rb rows (slab s, y) of one class; smem [row][ns]
 template <typename T, bool FROM_SLAB0>
-__global__ void k_xfwd(int Mt, int ns, int kfirst, int nrows, FftDesc d, const Cx<T> *__restrict__ tw, int rb,
+__global__ void k_xfwd(int Mt, int ns, int kfirst, int nrows, FftDesc d, const Tw<T> *__restrict__ tw, int rb,
                        const Cx<T> *__restrict__ zspec, const double *__restrict__ slab0, Cx<T> *__restrict__ rows)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -82,12 +82,11 @@ __global__ void k_xfwd(int Mt, int ns, int kfirst, int nrows, FftDesc d, const C
 }
 
 // ---- y pass with the scaling: CTA = (slab, chunk of xb columns); smem [y][p]
-// Class 0 (k3 = 0) reads the FP64 symbol table; other classes build
-//   4 pi / (ns^2 M3) * ex[kx] ex[ky] ez[k3] / (kappa^2 + k3^2).
+// Class 0 (k3 = 0) reads the FP64 symbol table, the other classes their own table
+// of 4 pi / (ns^2 M3) exp(-(1-eta) kappa^2 / 4 xi^2 - (1-eta_z) k3^2 / 4 xi^2) / (kappa^2 + k3^2).
 template <typename T, bool CLASS0>
-__global__ void k_yscale(int Mt, int ns, int kfirst, int count, FftDesc d, const Cx<T> *__restrict__ tw, int xb,
-                         Cx<T> *__restrict__ rows, const double *__restrict__ sym0, const T *__restrict__ ex,
-                         const T *__restrict__ ez, double dkap, double dk3, double norm)
+__global__ void k_yscale(int Mt, int ns, int kfirst, int count, FftDesc d, const Tw<T> *__restrict__ tw, int xb,
+                         Cx<T> *__restrict__ rows, const double *__restrict__ sym0, const T *__restrict__ symc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
@@ -102,18 +101,12 @@ __global__ void k_yscale(int Mt, int ns, int kfirst, int count, FftDesc d, const
     __syncthreads();
     Cx<T> *res = fft_smem<T>(a, b, d, xb, 1, xb, tw, -1);
     Cx<T> *oth = res == a ? b : a;
-    const int k3i = kfirst + s;
     for (int e = threadIdx.x; e < ns * xb; e += blockDim.x) {
         const int ky = e / xb, p = e % xb, kx = kx0 + p;
         T S = (T)0;
         if (kx < ns) {
-            if (CLASS0) {
-                S = (T)sym0[(size_t)ky * ns + kx];
-            } else {
-                const T kxv = (T)(dkap * signed_index(kx, ns)), kyv = (T)(dkap * signed_index(ky, ns));
-                const T k3v = (T)(dk3 * k3i);
-                S = (T)norm * ex[kx] * ex[ky] * ez[k3i] / (kxv * kxv + kyv * kyv + k3v * k3v);
-            }
+            if (CLASS0) S = (T)sym0[(size_t)ky * ns + kx];
+            else S = symc[((size_t)s * ns + ky) * ns + kx];
         }
         res[e] = scale(res[e], S);
     }
@@ -127,7 +120,7 @@ __global__ void k_yscale(int Mt, int ns, int kfirst, int count, FftDesc d, const
 
 // ---- x inverse: CTA = rb rows; inverse FFT along x, keep the first Mt points
 template <typename T, bool TO_SLAB0>
-__global__ void k_xinv(int Mt, int ns, int kfirst, int nrows, FftDesc d, const Cx<T> *__restrict__ tw, int rb,
+__global__ void k_xinv(int Mt, int ns, int kfirst, int nrows, FftDesc d, const Tw<T> *__restrict__ tw, int rb,
                        const Cx<T> *__restrict__ rows, Cx<T> *__restrict__ zspec, double *__restrict__ slab0)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -152,7 +145,7 @@ __global__ void k_xinv(int Mt, int ns, int kfirst, int nrows, FftDesc d, const C
 
 // ---- z inverse: Hermitian completion along z, inverse FFT, real part
 template <typename T>
-__global__ void k_zinv(int M3, int Mt, int K3, FftDesc d, const Cx<T> *__restrict__ tw, int xb,
+__global__ void k_zinv(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restrict__ tw, int xb,
                        const Cx<T> *__restrict__ zspec, const double *__restrict__ slab0, T *__restrict__ grid)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -201,6 +194,26 @@ __global__ void k_vico(int n0, double dkap, double R, double xi, double eta, dou
     sym[i] = norm * 4.0 * kPi * exp(-(1.0 - eta) * k2 / (4.0 * xi * xi)) * G;
 }
 
+// ---- k3 != 0 scaling tables (Eq. 3.5 with the Green's function of Eq. 3.6), one
+// per class, computed in FP64 and rounded once per mode.  Built on the fly in FP32
+// from per-axis factor tables, the symbol would carry those tables' roundings into
+// every mode that shares an index, a bias of the FP32 grid energy that does not
+// average out.
+template <typename T>
+__global__ void k_symbol(int ns, int count, int kfirst, double dkap, double dk3, double xi, double eta,
+                         double etaz, double norm, T *__restrict__ sym)
+{
+    const size_t total = (size_t)count * ns * ns;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int kx = (int)(i % ns), ky = (int)((i / ns) % ns), s = (int)(i / ((size_t)ns * ns));
+        const double ax = dkap * signed_index(kx, ns), ay = dkap * signed_index(ky, ns);
+        const double k3 = dk3 * (kfirst + s);
+        const double kap2 = ax * ax + ay * ay;
+        const double e = exp(-((1.0 - eta) * kap2 + (1.0 - etaz) * k3 * k3) / (4.0 * xi * xi));
+        sym[i] = (T)(norm * e / (kap2 + k3 * k3));
+    }
+}
+
 template <typename T> size_t cbytes() { return sizeof(Cx<T>); }
 
 }  // namespace
@@ -213,6 +226,24 @@ void launch_vico_table(se1p_plan *p, cudaStream_t s)
     const double norm = 1.0 / ((double)n0 * n0 * p->M3);
     k_vico<<<(n0 * n0 + 255) / 256, 256, 0, s>>>(n0, dkap, R, p->geo.xi, p->geo.eta, norm, p->b.sym0);
 }
+
+template <typename T> void launch_symbol_tables(se1p_plan *p, cudaStream_t s)
+{
+    const Geo &g = p->geo;
+    for (int c = 1; c < 3; ++c) {
+        const SlabClass &C = p->cls[c];
+        if (C.count == 0) continue;
+        const double dkap = 2.0 * kPi / (C.ns * g.h);
+        const double dk3 = 2.0 * kPi / g.L[2];
+        const double norm = 4.0 * kPi / ((double)p->M3 * C.ns * C.ns);
+        const size_t total = (size_t)C.count * C.ns * C.ns;
+        const int blocks = (int)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32);
+        k_symbol<T><<<blocks, 256, 0, s>>>(C.ns, C.count, C.kfirst, dkap, dk3, g.xi, g.eta, g.etaz, norm,
+                                           (T *)C.sym);
+    }
+}
+template void launch_symbol_tables<float>(se1p_plan *, cudaStream_t);
+template void launch_symbol_tables<double>(se1p_plan *, cudaStream_t);
 
 template <typename T> int configure_fourier_kernels(se1p_plan *p)
 {
@@ -235,47 +266,40 @@ template <typename T> int configure_fourier_kernels(se1p_plan *p)
 template <typename T> void launch_fourier(se1p_plan *p, cudaStream_t s)
 {
     const int Mt = p->Mt, M3 = p->M3, K3 = p->K3;
-    const Geo &g = p->geo;
     // z forward
     {
         const int xb = p->xb_z;
         const int nxc = (Mt + xb - 1) / xb;
         const size_t sm = 2 * (size_t)M3 * xb * cbytes<T>();
-        k_zfwd<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Cx<T> *)p->b.tw_z, xb, (const T *)p->b.grid,
+        k_zfwd<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb, (const T *)p->b.grid,
                                             (Cx<T> *)p->b.zspec, p->b.slab0_in);
     }
-    const double norm_base = 4.0 * kPi / M3;
     for (int c = 0; c < 3; ++c) {
         const SlabClass &C = p->cls[c];
         if (C.count == 0) continue;
         const int nrows = C.count * Mt;
-        const double dkap = 2.0 * kPi / (C.ns * g.h);
-        const double dk3 = 2.0 * kPi / g.L[2];
-        const double norm = norm_base / ((double)C.ns * C.ns);
         if (c == 0) {
             const size_t smx = 2 * (size_t)C.rb * C.ns * cbytes<double>();
             k_xfwd<double, true><<<(nrows + C.rb - 1) / C.rb, 256, smx, s>>>(
-                Mt, C.ns, 0, nrows, C.fd, (const Cx<double> *)C.tw, C.rb, nullptr, p->b.slab0_in, (Cx<double> *)C.rows);
+                Mt, C.ns, 0, nrows, C.fd, (const Tw<double> *)C.tw, C.rb, nullptr, p->b.slab0_in, (Cx<double> *)C.rows);
             const int nkc = (C.ns + C.xb - 1) / C.xb;
             const size_t smy = 2 * (size_t)C.ns * C.xb * cbytes<double>();
-            k_yscale<double, true><<<C.count * nkc, 256, smy, s>>>(Mt, C.ns, 0, C.count, C.fd, (const Cx<double> *)C.tw,
-                                                                  C.xb, (Cx<double> *)C.rows, p->b.sym0, nullptr,
-                                                                  nullptr, dkap, dk3, norm);
+            k_yscale<double, true><<<C.count * nkc, 256, smy, s>>>(Mt, C.ns, 0, C.count, C.fd, (const Tw<double> *)C.tw,
+                                                                  C.xb, (Cx<double> *)C.rows, p->b.sym0, nullptr);
             k_xinv<double, true><<<(nrows + C.rb - 1) / C.rb, 256, smx, s>>>(
-                Mt, C.ns, 0, nrows, C.fd, (const Cx<double> *)C.tw, C.rb, (const Cx<double> *)C.rows, nullptr,
+                Mt, C.ns, 0, nrows, C.fd, (const Tw<double> *)C.tw, C.rb, (const Cx<double> *)C.rows, nullptr,
                 p->b.slab0_out);
         } else {
             const size_t smx = 2 * (size_t)C.rb * C.ns * cbytes<T>();
             k_xfwd<T, false><<<(nrows + C.rb - 1) / C.rb, 256, smx, s>>>(
-                Mt, C.ns, C.kfirst, nrows, C.fd, (const Cx<T> *)C.tw, C.rb, (const Cx<T> *)p->b.zspec, nullptr,
+                Mt, C.ns, C.kfirst, nrows, C.fd, (const Tw<T> *)C.tw, C.rb, (const Cx<T> *)p->b.zspec, nullptr,
                 (Cx<T> *)C.rows);
             const int nkc = (C.ns + C.xb - 1) / C.xb;
             const size_t smy = 2 * (size_t)C.ns * C.xb * cbytes<T>();
-            k_yscale<T, false><<<C.count * nkc, 256, smy, s>>>(Mt, C.ns, C.kfirst, C.count, C.fd, (const Cx<T> *)C.tw,
-                                                              C.xb, (Cx<T> *)C.rows, nullptr, (const T *)C.ex,
-                                                              (const T *)p->b.ez, dkap, dk3, norm);
+            k_yscale<T, false><<<C.count * nkc, 256, smy, s>>>(Mt, C.ns, C.kfirst, C.count, C.fd, (const Tw<T> *)C.tw,
+                                                              C.xb, (Cx<T> *)C.rows, nullptr, (const T *)C.sym);
             k_xinv<T, false><<<(nrows + C.rb - 1) / C.rb, 256, smx, s>>>(
-                Mt, C.ns, C.kfirst, nrows, C.fd, (const Cx<T> *)C.tw, C.rb, (const Cx<T> *)C.rows, (Cx<T> *)p->b.zspec,
+                Mt, C.ns, C.kfirst, nrows, C.fd, (const Tw<T> *)C.tw, C.rb, (const Cx<T> *)C.rows, (Cx<T> *)p->b.zspec,
                 nullptr);
         }
     }
@@ -284,7 +308,7 @@ template <typename T> void launch_fourier(se1p_plan *p, cudaStream_t s)
         const int xb = p->xb_z;
         const int nxc = (Mt + xb - 1) / xb;
         const size_t sm = 2 * (size_t)M3 * xb * cbytes<T>();
-        k_zinv<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Cx<T> *)p->b.tw_z, xb,
+        k_zinv<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb,
                                             (const Cx<T> *)p->b.zspec, p->b.slab0_out, (T *)p->b.grid);
     }
 }

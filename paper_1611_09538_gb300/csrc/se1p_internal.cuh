@@ -42,6 +42,53 @@ template <typename T> __device__ __forceinline__ Cx<T> mul_si(Cx<T> a, int s)
 }
 template <typename T> __device__ __forceinline__ Cx<T> scale(Cx<T> a, T s) { return cx<T>(a.re * s, a.im * s); }
 
+// Butterfly constants c (cosines and sines of 2 pi m / R) as an exact double.  In FP32,
+// c is applied as hi + lo, so each product is rounded once from a nearly exact value:
+// a constant rounded to float would scale every butterfly output alike, a bias of the
+// transform's gain that does not average out (it shows in the energy, where the
+// self-interaction through the grid cancels against the self term).  FP64 uses c.
+template <typename T> __device__ __forceinline__ T mul_c(T v, double c)
+{
+    if constexpr (sizeof(T) == sizeof(double)) {
+        return v * c;
+    } else {
+        const float hi = (float)c, lo = (float)(c - (double)hi);
+        return fmaf(v, hi, v * lo);
+    }
+}
+// acc + v * c with c as above
+template <typename T> __device__ __forceinline__ T fma_c(T v, double c, T acc)
+{
+    if constexpr (sizeof(T) == sizeof(double)) {
+        return fma(v, c, acc);
+    } else {
+        const float hi = (float)c, lo = (float)(c - (double)hi);
+        return fmaf(v, hi, fmaf(v, lo, acc));
+    }
+}
+
+// Twiddle factor w^t = exp(-2 pi i t / n).  In FP32 each component is kept as hi + lo:
+// rounded alone, the few roots of unity that a whole pass uses (an early pass uses
+// only the 64th roots) have magnitudes that are off in the same direction, which
+// scales the transform by ~1 - 3e-8 and biases the grid energy.
+template <typename T> struct Tw;
+template <> struct __align__(16) Tw<float> { float re, im, lre, lim; };
+template <> struct __align__(16) Tw<double> { double re, im; };
+
+// v * w (s < 0, forward) or v * conj(w) (s > 0, inverse); FP32 adds the lo products first
+template <typename T> __device__ __forceinline__ Cx<T> tw_mul(Cx<T> v, Tw<T> w, int s)
+{
+    const T wi = s > 0 ? -w.im : w.im;
+    if constexpr (sizeof(T) == sizeof(double)) {
+        return cx<T>(v.re * w.re - v.im * wi, v.re * wi + v.im * w.re);
+    } else {
+        const float li = s > 0 ? -w.lim : w.lim;
+        const float re = fmaf(v.re, w.re, fmaf(-v.im, wi, fmaf(v.re, w.lre, -v.im * li)));
+        const float im = fmaf(v.re, wi, fmaf(v.im, w.re, fmaf(v.re, li, v.im * w.lre)));
+        return cx<float>(re, im);
+    }
+}
+
 // ------------------------------------------------------------------ FFT descriptor
 // A length-n transform factored into radices (applied first to last).  The
 // twiddle table holds w^t = exp(-2 pi i t / n), t = 0..n-1.
@@ -75,10 +122,13 @@ template <typename T> __device__ __forceinline__ void dft8(Cx<T> *v, int s)
     Cx<T> o[4] = {v[1], v[3], v[5], v[7]};
     dft4(e, s);
     dft4(o, s);
-    const T r = (T)0.70710678118654752440;
-    // w8^k = exp(s 2 pi i k / 8)
-    Cx<T> w1 = cx<T>(r, s * r), w3 = cx<T>(-r, s * r);
-    Cx<T> o1 = cmul(o[1], w1), o2 = mul_si(o[2], s), o3 = cmul(o[3], w3);
+    // w8^k = exp(s 2 pi i k / 8) = (+-1 + s i) / sqrt(2) for k = 1, 3:
+    // o w8 = ((+-a - s b) + i (+-b + s a)) / sqrt(2) for o = a + i b
+    constexpr double r = 0.70710678118654752440;
+    const T sa1 = s * o[1].re, sb1 = s * o[1].im, sa3 = s * o[3].re, sb3 = s * o[3].im;
+    const Cx<T> o1 = cx<T>(mul_c<T>(o[1].re - sb1, r), mul_c<T>(o[1].im + sa1, r));
+    const Cx<T> o3 = cx<T>(mul_c<T>(-o[3].re - sb3, r), mul_c<T>(-o[3].im + sa3, r));
+    const Cx<T> o2 = mul_si(o[2], s);
     v[0] = e[0] + o[0];
     v[4] = e[0] - o[0];
     v[1] = e[1] + o1;
@@ -94,22 +144,22 @@ template <typename T> __device__ __forceinline__ void dft8(Cx<T> *v, int s)
 template <typename T, int R> __device__ __forceinline__ void dft_odd(Cx<T> *v, int s)
 {
     constexpr int H = (R - 1) / 2;
-    T c[R], sn[R];
+    double c[R], sn[R];
     if constexpr (R == 3) {
-        const T cc[3] = {1, -0.5, -0.5};
-        const T ss[3] = {0, 0.86602540378443864676, -0.86602540378443864676};
+        const double cc[3] = {1, -0.5, -0.5};
+        const double ss[3] = {0, 0.86602540378443864676, -0.86602540378443864676};
         for (int m = 0; m < R; ++m) { c[m] = cc[m]; sn[m] = ss[m]; }
     } else if constexpr (R == 5) {
-        const T cc[5] = {1, 0.30901699437494742410, -0.80901699437494742410, -0.80901699437494742410,
-                         0.30901699437494742410};
-        const T ss[5] = {0, 0.95105651629515357212, 0.58778525229247312917, -0.58778525229247312917,
-                         -0.95105651629515357212};
+        const double cc[5] = {1, 0.30901699437494742410, -0.80901699437494742410, -0.80901699437494742410,
+                              0.30901699437494742410};
+        const double ss[5] = {0, 0.95105651629515357212, 0.58778525229247312917, -0.58778525229247312917,
+                              -0.95105651629515357212};
         for (int m = 0; m < R; ++m) { c[m] = cc[m]; sn[m] = ss[m]; }
     } else {
-        const T cc[7] = {1, 0.62348980185873353053, -0.22252093395631440429, -0.90096886790241912624,
-                         -0.90096886790241912624, -0.22252093395631440429, 0.62348980185873353053};
-        const T ss[7] = {0, 0.78183148246802980871, 0.97492791218182360702, 0.43388373911755812048,
-                         -0.43388373911755812048, -0.97492791218182360702, -0.78183148246802980871};
+        const double cc[7] = {1, 0.62348980185873353053, -0.22252093395631440429, -0.90096886790241912624,
+                              -0.90096886790241912624, -0.22252093395631440429, 0.62348980185873353053};
+        const double ss[7] = {0, 0.78183148246802980871, 0.97492791218182360702, 0.43388373911755812048,
+                              -0.43388373911755812048, -0.97492791218182360702, -0.78183148246802980871};
         for (int m = 0; m < R; ++m) { c[m] = cc[m]; sn[m] = ss[m]; }
     }
     Cx<T> sp[H], sm[H];
@@ -128,9 +178,9 @@ template <typename T, int R> __device__ __forceinline__ void dft_odd(Cx<T> *v, i
         Cx<T> accs = cx<T>(0, 0);
 #pragma unroll
         for (int j = 1; j <= H; ++j) {
-            int m = (j * k) % R;
-            acc = acc + scale(sp[j - 1], c[m]);
-            accs = accs + scale(sm[j - 1], sn[m]);
+            const int m = (j * k) % R;
+            acc = cx<T>(fma_c<T>(sp[j - 1].re, c[m], acc.re), fma_c<T>(sp[j - 1].im, c[m], acc.im));
+            accs = cx<T>(fma_c<T>(sm[j - 1].re, sn[m], accs.re), fma_c<T>(sm[j - 1].im, sn[m], accs.im));
         }
         v[k] = acc + mul_si(accs, s);
     }
@@ -141,7 +191,7 @@ template <typename T, int R> __device__ __forceinline__ void dft_odd(Cx<T> *v, i
 template <typename T, int R>
 __device__ __forceinline__ void stockham_pass(const Cx<T> *__restrict__ src, Cx<T> *__restrict__ dst, int n,
                                               int Ns, int npen, int sp, int sj,
-                                              const Cx<T> *__restrict__ tw, int s)
+                                              const Tw<T> *__restrict__ tw, int s)
 {
     const int nb = n / R;
     const int total = nb * npen;
@@ -161,11 +211,7 @@ __device__ __forceinline__ void stockham_pass(const Cx<T> *__restrict__ src, Cx<
         for (int r = 0; r < R; ++r) v[r] = src[p * sp + (i + r * nb) * sj];
         if (Ns > 1) {
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                Cx<T> w = tw[r * k * twmul];
-                if (s > 0) w.im = -w.im;
-                v[r] = cmul(v[r], w);
-            }
+            for (int r = 1; r < R; ++r) v[r] = tw_mul(v[r], tw[r * k * twmul], s);
         }
         if constexpr (R == 2) dft2(v);
         else if constexpr (R == 4) dft4(v, s);
@@ -182,7 +228,7 @@ __device__ __forceinline__ void stockham_pass(const Cx<T> *__restrict__ src, Cx<
 // holds the result.  Must be called by all threads of the block.
 template <typename T>
 __device__ Cx<T> *fft_smem(Cx<T> *a, Cx<T> *b, const FftDesc &d, int npen, int sp, int sj,
-                           const Cx<T> *__restrict__ tw, int s)
+                           const Tw<T> *__restrict__ tw, int s)
 {
     int Ns = 1;
     for (int st = 0; st < d.nrad; ++st) {
@@ -225,6 +271,11 @@ template <typename T> struct __align__(sizeof(T) == 4 ? 16 : 32) CellRec {
     T xh, yh, zh, q;
     T xl, yl, zl;
     int orig;
+};
+
+// FP64 factors applied to a gather's FP32 sums (potential; force in x, y; force in z).
+struct GatherScale {
+    double phi, fxy, fz;
 };
 
 // Geometry passed by value to kernels.

@@ -159,6 +159,31 @@ __global__ void k_scan(int nbins, int ncells, const int *__restrict__ counts, in
     }
 }
 
+// e^x in FP32 for the window exponents, x in [-87, 0]: e^x = 2^n e^r with
+// n = rint(x / ln 2) and r = x - n ln 2 (Cody and Waite's reduction: ln 2 in two
+// parts, the first with 8 trailing zero bits so that n * hi is exact for |n| < 256),
+// e^r by its Taylor series to r^8 (|r| <= ln 2 / 2, truncation < 3e-10), 2^n exact.
+// Every step rounds to nearest, so the result (within ~1.2 ulp) has no systematic
+// bias, which a window value must not have: the FP32 grid's self-interaction of
+// each charge would carry it into the energy.
+__device__ __forceinline__ float exp_window(float x)
+{
+    x = fmaxf(x, -87.0f);  // keeps 2^n normal; e^-87 ~ 1.6e-38 is below any window value used
+    const float n = rintf(x * 1.44269504088896341f);
+    float r = fmaf(n, -0.693145751953125f, x);
+    r = fmaf(n, -1.42860677e-06f, r);
+    float p = 2.48015873e-05f;  // 1/8!
+    p = fmaf(p, r, 1.98412698e-04f);
+    p = fmaf(p, r, 1.38888889e-03f);
+    p = fmaf(p, r, 8.33333333e-03f);
+    p = fmaf(p, r, 4.16666667e-02f);
+    p = fmaf(p, r, 1.66666667e-01f);
+    p = fmaf(p, r, 0.5f);
+    p = fmaf(p, r, 1.0f);
+    p = fmaf(p, r, 1.0f);
+    return p * __int_as_float(((int)n + 127) << 23);
+}
+
 // Scatter into bin order (with the window tables) and into cell order.
 template <typename T>
 __global__ void k_scatter(Geo g, int n, const double *__restrict__ xyzq, const int *__restrict__ bin_key,
@@ -178,23 +203,26 @@ __global__ void k_scatter(Geo g, int n, const double *__restrict__ xyzq, const i
     r.orig = i;
     r.q = (T)p.w;
     T *w = wts + (size_t)pos * 3 * g.P;
+    // Unnormalised windows exp(-alpha d^2): the normalisation (2 xi^2 / (pi eta))^{1/2}
+    // per axis is applied once, in FP64, after the gather, so that no rounded constant
+    // biases the FP32 grid (a bias there would not cancel against the self term).
     for (int a = 0; a < 3; ++a) {
         const double gg = s.t[a] - s.i0[a] - g.c;  // particle offset from the support centre, grid units
         r.g[a] = (T)gg;
         const double alpha = a < 2 ? g.alpha_xy : g.alpha_z;
-        const double wn = a < 2 ? g.wnorm_xy : g.wnorm_z;
         if constexpr (sizeof(T) == sizeof(double)) {
             for (int j = 0; j < g.P; ++j) {
                 const double d = gg - (double)(j - g.c);
-                w[a * g.P + j] = wn * exp(-alpha * d * d);
+                w[a * g.P + j] = exp(-alpha * d * d);
             }
         } else {
-            // FP32 window: |gg| < 1, so gg - (j - c) is exact to ~6e-8 absolute and the
-            // exponent's relative error stays below 4e-7 even at the support edge
-            const float gf = (float)gg, af = (float)alpha, wf = (float)wn;
+            // FP32 window: |gg| < 1, so gg - (j - c) is exact to ~6e-8 absolute; alpha is
+            // split into hi + lo so that its rounding does not bias every exponent alike
+            const float gf = (float)gg, ah = (float)alpha, al = (float)(alpha - (double)ah);
             for (int j = 0; j < g.P; ++j) {
                 const float d = gf - (float)(j - g.c);
-                w[a * g.P + j] = wf * expf(-af * d * d);
+                const float d2 = d * d;
+                w[a * g.P + j] = exp_window(-fmaf(ah, d2, al * d2));
             }
         }
     }
@@ -216,9 +244,10 @@ __global__ void k_scatter(Geo g, int n, const double *__restrict__ xyzq, const i
 
 // ------------------------------------------------------------------ gridding (Eq. 3.4)
 //
-// Output-stationary: one CTA owns an 8x8x8 tile of the grid and accumulates
-// every particle whose support overlaps it in registers (no atomics; every
-// grid point is written exactly once).  A 16-thread group covers the tile with
+// Output-stationary: a CTA owns an 8x8x8 tile of the grid and accumulates in
+// registers every particle whose support overlaps it; two CTAs share a tile
+// (alternate z bins) and add their partial tiles into the zeroed grid, one
+// atomic add per grid point each.  A 16-thread group covers the tile with
 // 2(z) x 2(y) x 8(x) points per thread, so each particle costs a thread 4
 // shared loads (its z, y and x window values) for 32 FMAs; the CTA's eight
 // groups take alternate particles and their partial tiles are added at the end.
@@ -229,6 +258,7 @@ __global__ void k_scatter(Geo g, int n, const double *__restrict__ xyzq, const i
 constexpr int kSpreadBatch = 128;
 constexpr int kSpreadGroups = 8;
 constexpr int kSpreadThreads = 16 * kSpreadGroups;
+constexpr int kSpreadSplit = 2;  // CTAs per tile, each taking every other z bin (atomic combine)
 
 template <typename T>
 __global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int *__restrict__ bin_start,
@@ -240,7 +270,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int *__r
     __shared__ T sq[kSpreadBatch];
     __shared__ __align__(16) T red[kSpreadGroups - 1][16][4][kBin];
     const int ntx = (g.Mt + kBin - 1) / kBin, nty = ntx;
-    const int tile = blockIdx.x;
+    const int tile = blockIdx.x / kSpreadSplit, part = blockIdx.x % kSpreadSplit;
     const int txi = tile % ntx, tyi = (tile / ntx) % nty, tzi = tile / (ntx * nty);
     const int x0 = txi * kBin, y0 = tyi * kBin, z0 = tzi * kBin;
     const int grp = threadIdx.x >> 4, tl = threadIdx.x & 15;
@@ -259,6 +289,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int *__r
     const bool allz = span + 2 * kBin > M3;
     int u = 0;
     int zb_iter = 0;
+    int zcount = 0;  // z bins seen so far; this CTA takes those with zcount % kSpreadSplit == part
     while (true) {
         int bz;
         if (allz) {
@@ -272,6 +303,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int *__r
             bz = s / kBin;
             u += min((bz + 1) * kBin, M3) - s;
         }
+        if ((zcount++ % kSpreadSplit) != part) continue;
         if (bx_lo > bx_hi || by_lo > by_hi) continue;
         for (int by = by_lo; by <= by_hi; ++by) {
             const int row = (bz * g.nby + by) * g.nbx;
@@ -342,7 +374,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int *__r
                     T v = acc[r][c];
 #pragma unroll
                     for (int q = 0; q < kSpreadGroups - 1; ++q) v += red[q][tl][r][c];
-                    if (x0 + c < g.Mt) dst[c] = v;
+                    if (x0 + c < g.Mt) atomicAdd(dst + c, v);  // the grid is zeroed before the launch
                 }
             }
         }
@@ -358,7 +390,7 @@ template <typename T, int PC>
 __global__ void __launch_bounds__(256) k_gather(Geo g, int n, const PartRec<T> *__restrict__ parts,
                                                 const T *__restrict__ wts, const T *__restrict__ grid,
                                                 double *__restrict__ phi, double *__restrict__ frc,
-                                                int flags)
+                                                int flags, GatherScale sc)
 {
     // flags: bit 0 adds the self term (Eq. 2.5); bit 1 writes the field -grad phi
     // instead of the force -q grad phi.
@@ -369,7 +401,6 @@ __global__ void __launch_bounds__(256) k_gather(Geo g, int n, const PartRec<T> *
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int P = PC > 0 ? PC : g.P;  // compile-time support width when PC > 0 (loops unroll)
     const int warps_total = gridDim.x * (blockDim.x >> 5);
-    const T h = (T)g.h, hz = (T)g.hz;
     for (int pi = blockIdx.x * (blockDim.x >> 5) + wib; pi < n; pi += warps_total) {
         const PartRec<T> r = parts[pi];
         const T *w = wts + (size_t)pi * 3 * P;
@@ -377,12 +408,12 @@ __global__ void __launch_bounds__(256) k_gather(Geo g, int n, const PartRec<T> *
         if (lane < P) {
             const T jc = (T)(lane - g.c);
             wx = w[lane];
-            wxd = wx * (r.g[0] - jc) * h;
+            wxd = wx * (r.g[0] - jc);
             const T wy = w[P + lane], wz = w[2 * P + lane];
             sy[wib][lane][0] = wy;
-            sy[wib][lane][1] = wy * (r.g[1] - jc) * h;
+            sy[wib][lane][1] = wy * (r.g[1] - jc);
             sz[wib][0][lane] = wz;
-            sz[wib][1][lane] = wz * (r.g[2] - jc) * hz;
+            sz[wib][1][lane] = wz * (r.g[2] - jc);
         } else if (lane < 34 - 0 && lane >= P && lane < 34) {
             sy[wib][lane][0] = (T)0;  // pad for the paired loads of an odd P
             sy[wib][lane][1] = (T)0;
@@ -427,16 +458,14 @@ __global__ void __launch_bounds__(256) k_gather(Geo g, int n, const PartRec<T> *
         T vfy = warp_sum(wx * afy);
         T vfz = warp_sum(wx * afz);
         if (lane == 0) {
-            const double h3 = g.h * g.h * g.hz;
             const double qd = (double)r.q;
-            double ph = h3 * (double)vphi;
+            double ph = sc.phi * (double)vphi;
             if (flags & 1) ph += -2.0 * g.xi / sqrt(kPi) * qd;
             phi[r.orig] = ph;
-            const double cxy = 4.0 * g.xi * g.xi / g.eta, cz = 4.0 * g.xi * g.xi / g.etaz;
             const double qf = (flags & 2) ? 1.0 : qd;
-            frc[3 * r.orig + 0] = qf * h3 * cxy * (double)vfx;
-            frc[3 * r.orig + 1] = qf * h3 * cxy * (double)vfy;
-            frc[3 * r.orig + 2] = qf * h3 * cz * (double)vfz;
+            frc[3 * r.orig + 0] = qf * sc.fxy * (double)vfx;
+            frc[3 * r.orig + 1] = qf * sc.fxy * (double)vfy;
+            frc[3 * r.orig + 2] = qf * sc.fz * (double)vfz;
         }
         __syncwarp();
     }
@@ -459,7 +488,7 @@ template <typename T, int PC>
 __global__ void __launch_bounds__(256) k_gather_vec(Geo g, int n, const PartRec<T> *__restrict__ parts,
                                                     const T *__restrict__ wts, const T *__restrict__ grid,
                                                     double *__restrict__ phi, double *__restrict__ frc,
-                                                    int flags)
+                                                    int flags, GatherScale sc)
 {
     constexpr int V = 16 / sizeof(T);
     constexpr int NQ = (PC + V - 1 + V - 1) / V;
@@ -472,7 +501,6 @@ __global__ void __launch_bounds__(256) k_gather_vec(Geo g, int n, const PartRec<
     const int rr = lane / NQ, qv = lane - rr * NQ;  // row within the request, vector index
     const bool active = rr < RPR;
     const int warps_total = gridDim.x * (blockDim.x >> 5);
-    const T h = (T)g.h, hz = (T)g.hz;
     for (int pi = blockIdx.x * (blockDim.x >> 5) + wib; pi < n; pi += warps_total) {
         const PartRec<T> r = parts[pi];
         const T *w = wts + (size_t)pi * 3 * PC;
@@ -480,7 +508,7 @@ __global__ void __launch_bounds__(256) k_gather_vec(Geo g, int n, const PartRec<
             T wy = 0, wyd = 0;
             if (j < PC) {
                 wy = w[PC + j];
-                wyd = wy * (r.g[1] - (T)(j - g.c)) * h;
+                wyd = wy * (r.g[1] - (T)(j - g.c));
             }
             sy[wib][0][j] = wy;
             sy[wib][1][j] = wyd;
@@ -488,7 +516,7 @@ __global__ void __launch_bounds__(256) k_gather_vec(Geo g, int n, const PartRec<
         if (lane < PC) {
             const T wz = w[2 * PC + lane];
             sz[wib][0][lane] = wz;
-            sz[wib][1][lane] = wz * (r.g[2] - (T)(lane - g.c)) * hz;
+            sz[wib][1][lane] = wz * (r.g[2] - (T)(lane - g.c));
         }
         // this lane's V x points: window index rel = base + V qv + e - i0
         const int base = r.i0[0] & ~(V - 1);
@@ -498,7 +526,7 @@ __global__ void __launch_bounds__(256) k_gather_vec(Geo g, int n, const PartRec<
             const int rel = base + V * qv + e - r.i0[0];
             const bool in = active && rel >= 0 && rel < PC;
             wx[e] = in ? w[rel] : (T)0;
-            wxd[e] = in ? wx[e] * (r.g[0] - (T)(rel - g.c)) * h : (T)0;
+            wxd[e] = in ? wx[e] * (r.g[0] - (T)(rel - g.c)) : (T)0;
         }
         // only vectors holding at least one window point are read: such a vector starts at a
         // multiple of V below i0 + P <= Mt and so ends inside the row (Mt % V == 0)
@@ -531,16 +559,14 @@ __global__ void __launch_bounds__(256) k_gather_vec(Geo g, int n, const PartRec<
         }
         const T vphi = warp_sum(aphi), vfx = warp_sum(afx), vfy = warp_sum(afy), vfz = warp_sum(afz);
         if (lane == 0) {
-            const double h3 = g.h * g.h * g.hz;
             const double qd = (double)r.q;
-            double ph = h3 * (double)vphi;
+            double ph = sc.phi * (double)vphi;
             if (flags & 1) ph += -2.0 * g.xi / sqrt(kPi) * qd;
             phi[r.orig] = ph;
-            const double cxy = 4.0 * g.xi * g.xi / g.eta, cz = 4.0 * g.xi * g.xi / g.etaz;
             const double qf = (flags & 2) ? 1.0 : qd;
-            frc[3 * r.orig + 0] = qf * h3 * cxy * (double)vfx;
-            frc[3 * r.orig + 1] = qf * h3 * cxy * (double)vfy;
-            frc[3 * r.orig + 2] = qf * h3 * cz * (double)vfz;
+            frc[3 * r.orig + 0] = qf * sc.fxy * (double)vfx;
+            frc[3 * r.orig + 1] = qf * sc.fxy * (double)vfy;
+            frc[3 * r.orig + 2] = qf * sc.fz * (double)vfz;
         }
         __syncwarp();
     }
@@ -605,10 +631,10 @@ __global__ void k_vjp_combine(int n, const double *__restrict__ q, const double 
 }
 
 template <typename TS, typename TD>
-__global__ void k_convert(size_t n, const TS *__restrict__ src, TD *__restrict__ dst)
+__global__ void k_convert(size_t n, const TS *__restrict__ src, TD *__restrict__ dst, double scale)
 {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        dst[i] = (TD)src[i];
+        dst[i] = (TD)((double)src[i] * scale);
 }
 
 inline int blocks_for(size_t n, int bs, int cap = 1 << 20)
@@ -650,7 +676,8 @@ template <typename T> void launch_spread(se1p_plan *p, cudaStream_t s)
     const Geo &g = p->geo;
     const int nt = (g.Mt + kBin - 1) / kBin;
     const int ntz = (g.M3 + kBin - 1) / kBin;
-    k_spread<T><<<nt * nt * ntz, kSpreadThreads, 0, s>>>(g, p->b.starts, (const PartRec<T> *)p->b.parts,
+    cudaMemsetAsync(p->b.grid, 0, sizeof(T) * (size_t)g.M3 * g.Mt * g.Mt, s);
+    k_spread<T><<<nt * nt * ntz * kSpreadSplit, kSpreadThreads, 0, s>>>(g, p->b.starts, (const PartRec<T> *)p->b.parts,
                                               (const T *)p->b.wts, (T *)p->b.grid);
 }
 
@@ -662,17 +689,26 @@ void launch_gather(se1p_plan *p, int n, const void *grid, double *phi, double *f
     int blocks = (n + warps_per_block - 1) / warps_per_block;
     if (blocks > 152 * 64) blocks = 152 * 64;
     const Geo &g = p->geo;
+    // FP64 constants applied to the FP32 sums: quadrature weight h^3, the window
+    // normalisation of the gather (and of the spread when the grid is this plan's own
+    // unnormalised spread, flag bit 2), and for the force 4 xi^2 / eta times the grid
+    // step that turns the offsets (grid units) into lengths
+    const double w3 = g.wnorm_xy * g.wnorm_xy * g.wnorm_z;
+    GatherScale sc;
+    sc.phi = g.h * g.h * g.hz * w3 * ((flags & 4) ? w3 : 1.0);
+    sc.fxy = sc.phi * 4.0 * g.xi * g.xi / g.eta * g.h;
+    sc.fz = sc.phi * 4.0 * g.xi * g.xi / g.etaz * g.hz;
     const PartRec<T> *pr = (const PartRec<T> *)p->b.parts;
     const T *w = (const T *)p->b.wts;
     const T *gr = (const T *)grid;
     const int nt = 32 * warps_per_block;
     constexpr int V = 16 / sizeof(T);
     const bool vec = g.Mt % V == 0;
-    if (vec && g.P == 24) k_gather_vec<T, 24><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags);
-    else if (vec && g.P == 16) k_gather_vec<T, 16><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags);
-    else if (g.P == 24) k_gather<T, 24><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags);
-    else if (g.P == 16) k_gather<T, 16><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags);
-    else k_gather<T, 0><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags);
+    if (vec && g.P == 24) k_gather_vec<T, 24><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
+    else if (vec && g.P == 16) k_gather_vec<T, 16><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
+    else if (g.P == 24) k_gather<T, 24><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
+    else if (g.P == 16) k_gather<T, 16><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
+    else k_gather<T, 0><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
 }
 
 void launch_vjp_combine(int n, const double *q, const double *v, const double *Eq, const double *phiv,
@@ -687,16 +723,17 @@ void launch_finalize(se1p_plan *p, int n, double *phi, double *frc, double *ener
     if (energy) k_energy_final<<<1, 256, 0, s>>>(p->b.epart, kEnergyBlocks, energy);
 }
 
-template <typename T> void launch_grid_to_double(se1p_plan *p, const void *src, double *dst, cudaStream_t s)
+template <typename T>
+void launch_grid_to_double(se1p_plan *p, const void *src, double *dst, double scale, cudaStream_t s)
 {
     const size_t n = (size_t)p->M3 * p->Mt * p->Mt;
-    k_convert<T, double><<<blocks_for(n, 256, 4096), 256, 0, s>>>(n, (const T *)src, dst);
+    k_convert<T, double><<<blocks_for(n, 256, 4096), 256, 0, s>>>(n, (const T *)src, dst, scale);
 }
 
 template <typename T> void launch_grid_from_double(se1p_plan *p, const double *src, void *dst, cudaStream_t s)
 {
     const size_t n = (size_t)p->M3 * p->Mt * p->Mt;
-    k_convert<double, T><<<blocks_for(n, 256, 4096), 256, 0, s>>>(n, src, (T *)dst);
+    k_convert<double, T><<<blocks_for(n, 256, 4096), 256, 0, s>>>(n, src, (T *)dst, 1.0);
 }
 
 template <typename T> int configure_particle_kernels() { return 0; }
@@ -706,7 +743,7 @@ template <typename T> int configure_particle_kernels() { return 0; }
     template void launch_sort_scatter<T>(se1p_plan *, int, cudaStream_t);                                   \
     template void launch_spread<T>(se1p_plan *, cudaStream_t);                                              \
     template void launch_gather<T>(se1p_plan *, int, const void *, double *, double *, int, cudaStream_t);  \
-    template void launch_grid_to_double<T>(se1p_plan *, const void *, double *, cudaStream_t);             \
+    template void launch_grid_to_double<T>(se1p_plan *, const void *, double *, double, cudaStream_t);           \
     template void launch_grid_from_double<T>(se1p_plan *, const double *, void *, cudaStream_t);           \
     template int configure_particle_kernels<T>();
 SE1P_INST(float)

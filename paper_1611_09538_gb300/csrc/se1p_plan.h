@@ -18,7 +18,7 @@ struct SlabClass {
     FftDesc fd{};     // FFT of length ns
     void *tw = nullptr;     // twiddles (Cx<T>, or Cx<double> for class 0)
     void *rows = nullptr;   // [count][Mt][ns] complex work rows
-    void *ex = nullptr;     // exp(-(1-eta) kappa_i^2 / 4 xi^2), i = 0..ns-1 (T)
+    void *sym = nullptr;    // classes 1, 2: scaling symbol incl. normalisation, [count][ns][ns] (T)
     int rb = 1;             // rows per CTA in the x passes
     int xb = 1;             // columns per CTA in the y pass
 };
@@ -29,7 +29,6 @@ struct Buffers {
     double *slab0_in = nullptr;  // k3 = 0 coefficient of H, [Mt][Mt]
     double *slab0_out = nullptr; // k3 = 0 coefficient of Ht, [Mt][Mt]
     double *sym0 = nullptr;      // k3 = 0 scaling incl. normalisation, [n0][n0]
-    void *ez = nullptr;          // exp(-(1-etaz) k3^2 / 4 xi^2) / (k3 normalisation), [K3] (T)
     void *tw_z = nullptr;        // Cx<T> [M3]
     double *xyzq = nullptr;      // sanitised caller-order particles [n_max][4]
     int *bin_key = nullptr, *cell_key = nullptr;
@@ -88,7 +87,8 @@ template <typename T> void launch_gather(se1p_plan *p, int n, const void *grid, 
 void launch_vjp_combine(int n, const double *q, const double *v, const double *Eq, const double *phiv,
                         const double *Ev, double *grad_x, double *grad_q, cudaStream_t s);
 void launch_finalize(se1p_plan *p, int n, double *phi, double *frc, double *energy, cudaStream_t s);
-template <typename T> void launch_grid_to_double(se1p_plan *p, const void *src, double *dst, cudaStream_t s);
+template <typename T>
+void launch_grid_to_double(se1p_plan *p, const void *src, double *dst, double scale, cudaStream_t s);
 template <typename T> void launch_grid_from_double(se1p_plan *p, const double *src, void *dst, cudaStream_t s);
 template <typename T> int configure_particle_kernels();
 
@@ -96,6 +96,7 @@ template <typename T> int configure_particle_kernels();
 template <typename T> void launch_fourier(se1p_plan *p, cudaStream_t s);
 template <typename T> int configure_fourier_kernels(se1p_plan *p);
 void launch_vico_table(se1p_plan *p, cudaStream_t s);
+template <typename T> void launch_symbol_tables(se1p_plan *p, cudaStream_t s);
 
 // ---- se1p_real.cu
 // flags: bit 0 accumulates into phi/frc (else they are overwritten), bit 1 writes the field

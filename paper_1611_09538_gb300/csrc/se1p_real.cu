@@ -10,23 +10,41 @@ namespace se1p {
 
 namespace {
 
-template <typename T> __device__ __forceinline__ T erfc_t(T v);
-template <> __device__ __forceinline__ float erfc_t<float>(float v) { return erfcf(v); }
-template <> __device__ __forceinline__ double erfc_t<double>(double v) { return erfc(v); }
-template <typename T> __device__ __forceinline__ T exp_t(T v);
-template <> __device__ __forceinline__ float exp_t<float>(float v) { return exp2f(v * 1.4426950408889634f); }
-template <> __device__ __forceinline__ double exp_t<double>(double v) { return exp(v); }
-
 constexpr int kRealWarps = 4;  // warps per CTA (warps work independently)
 constexpr int kRealSplit = 4;  // warps sharing one group of 32 targets (source rows split between them)
 constexpr int kCand = 96;      // per-warp candidate list (flushed at >= 64)
+
+// Hardware approximations with denormals flushed (arguments here are far from the
+// denormal range: r^2 >= ~1e-14, exp(-xi^2 r^2) >= ~1e-11, 1 + x/2 >= 1).
+__device__ __forceinline__ float rsqrt_hw(float v)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v));
+    return y;
+}
+__device__ __forceinline__ float ex2_hw(float v)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v));
+    return y;
+}
+__device__ __forceinline__ float rcp_hw(float v)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v));
+    return y;
+}
+
+template <typename T> __device__ __forceinline__ T exp_t(T v);
+template <> __device__ __forceinline__ float exp_t<float>(float v) { return ex2_hw(v * 1.4426950408889634f); }
+template <> __device__ __forceinline__ double exp_t<double>(double v) { return exp(v); }
 
 template <typename T> __device__ __forceinline__ T rsqrt_t(T v);
 // 1/sqrt with one Newton step after the hardware estimate, so that r = r2 / sqrt(r2)
 // is within ~1 ulp (erfc(xi r) near rc amplifies the relative error of r ~10x).
 template <> __device__ __forceinline__ float rsqrt_t<float>(float v)
 {
-    const float y = rsqrtf(v);
+    const float y = rsqrt_hw(v);
     return y * fmaf(-0.5f * v * y, y, 1.5f);
 }
 template <> __device__ __forceinline__ double rsqrt_t<double>(double v) { return rsqrt(v); }
@@ -41,7 +59,7 @@ __device__ __forceinline__ float erfc_from_exp(float x, float E)
                          -2.097116850e-01f, -3.031409504e-02f, 1.127779386e-01f, -1.429198095e-02f,
                          -6.719807144e-02f, 2.960473828e-02f, 3.436364278e-02f};
     const float d = fmaf(kErfcxP, x, 1.0f);
-    float t = __fdividef(1.0f, d);
+    float t = rcp_hw(d);
     t = t * fmaf(-d, t, 2.0f);  // one Newton step on the hardware reciprocal
     const float u = t - kErfcxTc;
     // Estrin's scheme: dependency depth 4 instead of 10 for Horner
@@ -54,13 +72,51 @@ __device__ __forceinline__ float erfc_from_exp(float x, float E)
 }
 __device__ __forceinline__ double erfc_from_exp(double x, double) { return erfc(x); }
 
-// z displacement of target m from a source image shifted by sh (a multiple of L3).
-// The shift is applied first to whichever coordinate lies at the far wall, so the
-// large cancellation (z close to +-L3) is exact (Sterbenz) and only the final,
-// small difference is rounded; lo parts then restore the FP64 coordinates.
-template <typename T> __device__ __forceinline__ T image_dz(T zm, T zs, T sh)
+// A source (with its z image shift folded in) or a target, in shared memory:
+// hi parts and the charge first, so the hi float4 doubles as the phase-1 copy.
+template <typename T> struct __align__(sizeof(T) == 4 ? 16 : 32) PairRec {
+    T xh, yh, zh, q;
+    T xl, yl, zl, pad;
+};
+
+// Displacement target - source from hi + lo parts.  Each hi difference is one
+// rounding of a difference (exact when the two are within a factor 2, Sterbenz),
+// the lo parts restore the FP64 coordinates to ~1e-15.  In FP64 only z carries a
+// lo part (the rounding error of the image shift).
+template <typename T>
+__device__ __forceinline__ void displacement(const PairRec<T> &a, const PairRec<T> &c, T &dx, T &dy, T &dz)
 {
-    return sh > (T)0 ? (zm - sh) - zs : (sh < (T)0 ? zm - (zs + sh) : zm - zs);
+    dx = a.xh - c.xh;
+    dy = a.yh - c.yh;
+    dz = a.zh - c.zh;
+    if constexpr (sizeof(T) < sizeof(double)) {
+        dx += a.xl - c.xl;
+        dy += a.yl - c.yl;
+    }
+    dz += a.zl - c.zl;
+}
+
+// Contribution of one source of charge qs at displacement d (Eq. 2.2 and its
+// gradient, Eq. 3.22), added to (ph, fx, fy, fz).  Pairs with r = 0 (the target
+// itself; distinct coincident charges are outside the sum's domain) or r > rc
+// add nothing.  Branch-free: rejected pairs run on r^2 = rc^2 with zero charge.
+template <typename T>
+__device__ __forceinline__ void pair_terms(T dx, T dy, T dz, T qs, T rc2, T xi, T xi2, T two_xi_sqpi, T &ph,
+                                           T &fx, T &fy, T &fz)
+{
+    const T r2 = dx * dx + dy * dy + dz * dz;
+    const bool ok = r2 > (T)0 && r2 <= rc2;
+    const T r2s = ok ? r2 : rc2;
+    const T qq = ok ? qs : (T)0;
+    const T rinv = rsqrt_t<T>(r2s);
+    const T r = r2s * rinv;
+    const T E = exp_t<T>(-xi2 * r2s);
+    const T e = erfc_from_exp(xi * r, E) * rinv;
+    ph += qq * e;
+    const T fs = qq * (two_xi_sqpi * E + e) * rinv * rinv;
+    fx += fs * dx;
+    fy += fs * dy;
+    fz += fs * dz;
 }
 
 // Real-space sum, warp-centric.  Warp w owns the 32 consecutive targets
@@ -68,14 +124,18 @@ template <typename T> __device__ __forceinline__ T image_dz(T zm, T zs, T sh)
 // targets occupy a small box of cells.  Sources come from that box expanded by
 // S = ceil(rc / cell edge) cells per axis; for each (y, z) cell row the x-range
 // is contiguous in cell order, i.e. one source range; z images come from
-// unwrapped rows nz_u = nz + wrap * ncz, shifted by wrap * L3.
+// unwrapped rows nz_u = nz + wrap * ncz, shifted by wrap * L3 (folded into the
+// source's z as an exact hi + lo sum, Fast2Sum).
 //
 // Sources are read 32 at a time, one per lane, and tested in parallel against
 // the warp's target bounding box grown by rc; the survivors are compacted by
-// ballot into a per-warp list.  When the list holds >= 32 candidates every lane
-// marks (cheap hi-part test, threshold widened by 1e-5) the candidates within rc
-// of its own target, then walks its marks: exact displacement (hi + lo, shift
-// hi + lo), exact r <= rc test, erfc and exp.
+// ballot into a per-warp list.  When the list holds >= 64 candidates:
+//   phase 1: every lane marks the candidates within rc of its own target (float
+//            test on the hi parts, threshold widened so no true pair is lost);
+//   phase 2: every lane walks its own marks: hi + lo displacement, the exact
+//            r <= rc test and the pair terms, branch-free.
+// (Spreading the marks of busy lanes over idle ones through shared memory was
+// measured slower: the bookkeeping per pair costs more than the idle lanes.)
 template <typename T>
 __global__ void __launch_bounds__(32 * kRealWarps) k_real(Geo g, int n, const int *__restrict__ cell_start,
                                                           const CellRec<T> *__restrict__ cells,
@@ -83,27 +143,36 @@ __global__ void __launch_bounds__(32 * kRealWarps) k_real(Geo g, int n, const in
                                                           double *__restrict__ phi, double *__restrict__ frc,
                                                           int accumulate)
 {
-    __shared__ CellRec<T> cand[kRealWarps][kCand];
-    __shared__ float4 cpos[kRealWarps][kCand];  // phase-1 copy: x, y, z + shift (float), q
-    __shared__ T cshh[kRealWarps][kCand], cshl[kRealWarps][kCand];
+    __shared__ PairRec<T> cand[kRealWarps][kCand];
+    __shared__ float4 cposd[sizeof(T) == 4 ? 1 : kRealWarps][sizeof(T) == 4 ? 1 : kCand];  // FP64: float copy
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * kRealWarps + wib;
     const int warp = gw / kRealSplit, part = gw % kRealSplit;  // target group, share of the source rows
     const int t = warp * 32 + lane;
     if (warp * 32 >= n) return;  // whole warp beyond the particles
     const bool valid = t < n;
-    CellRec<T> me;
+    PairRec<T> me;
+    int orig = -1;
+    T qme = (T)0;
     int cx = 0, cy = 0, cz = 0;
     if (valid) {
-        me = cells[t];
-        const int cell = cell_key[me.orig];
+        const CellRec<T> r = cells[t];
+        me.xh = r.xh;
+        me.yh = r.yh;
+        me.zh = r.zh;
+        me.xl = r.xl;
+        me.yl = r.yl;
+        me.zl = r.zl;
+        qme = r.q;
+        orig = r.orig;
+        const int cell = cell_key[orig];
         cx = cell % g.ncx;
         cy = (cell / g.ncx) % g.ncy;
         cz = cell / (g.ncx * g.ncy);
     } else {
-        me.xh = me.yh = me.zh = me.q = me.xl = me.yl = me.zl = (T)0;
-        me.orig = -1;
+        me.xh = me.yh = me.zh = me.xl = me.yl = me.zl = (T)0;
     }
+    me.q = me.pad = (T)0;
     const unsigned full = 0xffffffffu;
     const int big = 1 << 30;
     // box of the warp's target cells (invalid lanes do not widen it)
@@ -127,13 +196,13 @@ __global__ void __launch_bounds__(32 * kRealWarps) k_real(Geo g, int n, const in
     const T xi = (T)g.xi, rc2 = (T)g.rc2;
     const T two_xi_sqpi = (T)(2.0 * g.xi / sqrt(kPi));
     const T xi2 = (T)(g.xi * g.xi);
-    CellRec<T> *cl = cand[wib];
-    T *ch = cshh[wib], *cll = cshl[wib];
+    PairRec<T> *cl = cand[wib];
+    const float4 *cp = sizeof(T) == 4 ? reinterpret_cast<const float4 *>(cl) : cposd[sizeof(T) == 4 ? 0 : wib];
+    constexpr int cps = sizeof(T) == 4 ? 2 : 1;  // float4 stride of the phase-1 copy
     const unsigned lt_mask = (1u << lane) - 1u;
     double aphi = 0, afx = 0, afy = 0, afz = 0;
     int ncand = 0;
 
-    float4 *cp = cpos[wib];
     const float mxf = (float)me.xh, myf = (float)me.yh, mzf = (float)me.zh;
     // phase-1 threshold: rc widened by 1e-5 rc plus a few float ulps of the box size, so the
     // float test (coordinates and image shift rounded to float) never drops a true pair
@@ -147,56 +216,35 @@ __global__ void __launch_bounds__(32 * kRealWarps) k_real(Geo g, int n, const in
         if (valid) {
             const int n0 = min(nc, 32), n1 = min(nc, 64);
             for (int j = 0; j < n0; ++j) {
-                const float4 c = cp[j];
+                const float4 c = cp[j * cps];
                 const float dx = mxf - c.x, dy = myf - c.y, dz = mzf - c.z;
                 if (dx * dx + dy * dy + dz * dz <= rc2wf) m0 |= 1u << j;
             }
             for (int j = 32; j < n1; ++j) {
-                const float4 c = cp[j];
+                const float4 c = cp[j * cps];
                 const float dx = mxf - c.x, dy = myf - c.y, dz = mzf - c.z;
                 if (dx * dx + dy * dy + dz * dz <= rc2wf) m1 |= 1u << (j - 32);
             }
             for (int j = 64; j < nc; ++j) {
-                const float4 c = cp[j];
+                const float4 c = cp[j * cps];
                 const float dx = mxf - c.x, dy = myf - c.y, dz = mzf - c.z;
                 if (dx * dx + dy * dy + dz * dz <= rc2wf) m2 |= 1u << (j - 64);
             }
         }
-        // phase 2: exact displacement and the pair terms, each lane walking its own marks
+        // phase 2: this lane's marks, word by word
         T pphi = 0, pfx = 0, pfy = 0, pfz = 0;
-        while (m0 | m1 | m2) {
-            int j;
-            if (m0) {
-                j = __ffs(m0) - 1;
-                m0 &= m0 - 1u;
-            } else if (m1) {
-                j = 32 + __ffs(m1) - 1;
-                m1 &= m1 - 1u;
-            } else {
-                j = 64 + __ffs(m2) - 1;
-                m2 &= m2 - 1u;
+        auto walk = [&](unsigned m, int j0) {
+            while (m) {
+                const int j = j0 + __ffs(m) - 1;
+                m &= m - 1u;
+                T dx, dy, dz;
+                displacement(me, cl[j], dx, dy, dz);
+                pair_terms(dx, dy, dz, cl[j].q, rc2, xi, xi2, two_xi_sqpi, pphi, pfx, pfy, pfz);
             }
-            const CellRec<T> sr = cl[j];
-            const T sh = ch[j];
-            if (sr.orig == me.orig && sh == (T)0) continue;  // the target itself
-            T dx = me.xh - sr.xh, dy = me.yh - sr.yh, dz = image_dz(me.zh, sr.zh, sh);
-            if constexpr (sizeof(T) < sizeof(double)) {
-                dx += me.xl - sr.xl;
-                dy += me.yl - sr.yl;
-                dz += (me.zl - sr.zl) - cll[j];
-            }
-            const T r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 > rc2) continue;
-            const T rinv = rsqrt_t<T>(r2);
-            const T r = r2 * rinv;
-            const T E = exp_t<T>(-xi2 * r2);
-            const T e = erfc_from_exp(xi * r, E) * rinv;
-            pphi += sr.q * e;
-            const T fs = sr.q * (two_xi_sqpi * E + e) * rinv * rinv;
-            pfx += fs * dx;
-            pfy += fs * dy;
-            pfz += fs * dz;
-        }
+        };
+        walk(m0, 0);
+        walk(m1, 32);
+        walk(m2, 64);
         aphi += (double)pphi;
         afx += (double)pfx;
         afy += (double)pfy;
@@ -213,34 +261,45 @@ __global__ void __launch_bounds__(32 * kRealWarps) k_real(Geo g, int n, const in
         const double shd = wrap * g.L[2];
         const T sh = (T)shd, shl = (T)(shd - (double)sh);
         const float shf = (float)shd;
-        {
-            const int row = (nz * g.ncy + ny) * g.ncx;
-            const int sbeg = cell_start[row + nx_lo], send = cell_start[row + nx_hi + 1];
-            for (int s0 = sbeg; s0 < send; s0 += 32) {
-                const int si = s0 + lane;
-                bool keep = false;
-                CellRec<T> rec;
-                if (si < send) {
-                    rec = cells[si];
-                    const float sx = (float)rec.xh, sy = (float)rec.yh, sz = (float)rec.zh + shf;
-                    const float ex = fmaxf(fmaxf(bx0 - sx, sx - bx1), 0.0f);
-                    const float ey = fmaxf(fmaxf(by0 - sy, sy - by1), 0.0f);
-                    const float ez = fmaxf(fmaxf(bz0 - sz, sz - bz1), 0.0f);
-                    keep = ex * ex + ey * ey + ez * ez <= rbox2;
-                }
-                const unsigned bal = __ballot_sync(full, keep);
-                if (keep) {
-                    const int pos = ncand + __popc(bal & lt_mask);
-                    cl[pos] = rec;
-                    ch[pos] = sh;
-                    cll[pos] = shl;
-                    cp[pos] = make_float4((float)rec.xh, (float)rec.yh, (float)rec.zh + shf, (float)rec.q);
-                }
-                ncand += __popc(bal);
-                if (ncand >= 64) {
-                    process(ncand);
-                    ncand = 0;
-                }
+        const int row = (nz * g.ncy + ny) * g.ncx;
+        const int sbeg = cell_start[row + nx_lo], send = cell_start[row + nx_hi + 1];
+        for (int s0 = sbeg; s0 < send; s0 += 32) {
+            const int si = s0 + lane;
+            bool keep = false;
+            CellRec<T> rec;
+            if (si < send) {
+                rec = cells[si];
+                const float sx = (float)rec.xh, sy = (float)rec.yh, sz = (float)rec.zh + shf;
+                const float ex = fmaxf(fmaxf(bx0 - sx, sx - bx1), 0.0f);
+                const float ey = fmaxf(fmaxf(by0 - sy, sy - by1), 0.0f);
+                const float ez = fmaxf(fmaxf(bz0 - sz, sz - bz1), 0.0f);
+                keep = ex * ex + ey * ey + ez * ez <= rbox2;
+            }
+            const unsigned bal = __ballot_sync(full, keep);
+            if (keep) {
+                const int pos = ncand + __popc(bal & lt_mask);
+                // z + shift as hi + lo: Fast2Sum (|sh| > |zh| whenever sh != 0) gives the
+                // rounding error of the hi sum exactly
+                const T zs = sh + rec.zh;
+                const T zerr = rec.zh - (zs - sh);
+                PairRec<T> c;
+                c.xh = rec.xh;
+                c.yh = rec.yh;
+                c.zh = zs;
+                c.q = rec.q;
+                c.xl = rec.xl;
+                c.yl = rec.yl;
+                c.zl = (rec.zl + shl) + zerr;
+                c.pad = (T)0;
+                cl[pos] = c;
+                if constexpr (sizeof(T) != 4)
+                    cposd[sizeof(T) == 4 ? 0 : wib][sizeof(T) == 4 ? 0 : pos] =
+                        make_float4((float)rec.xh, (float)rec.yh, (float)rec.zh + shf, (float)rec.q);
+            }
+            ncand += __popc(bal);
+            if (ncand >= 64) {
+                process(ncand);
+                ncand = 0;
             }
         }
     }
@@ -248,14 +307,12 @@ __global__ void __launch_bounds__(32 * kRealWarps) k_real(Geo g, int n, const in
     if (valid) {
         // the kRealSplit warps of a target group combine through FP64 atomics
         // (outputs are zeroed beforehand when not accumulating)
-        const double qm = (accumulate & 2) ? 1.0 : (double)me.q;  // bit 1: field instead of force
-        const int o = me.orig;
-        atomicAdd(phi + o, aphi);
-        atomicAdd(frc + 3 * o, qm * afx);
-        atomicAdd(frc + 3 * o + 1, qm * afy);
-        atomicAdd(frc + 3 * o + 2, qm * afz);
+        const double qm = (accumulate & 2) ? 1.0 : (double)qme;  // bit 1: field instead of force
+        atomicAdd(phi + orig, aphi);
+        atomicAdd(frc + 3 * orig, qm * afx);
+        atomicAdd(frc + 3 * orig + 1, qm * afy);
+        atomicAdd(frc + 3 * orig + 2, qm * afz);
     }
-    (void)accumulate;
 }
 
 }  // namespace

@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-throughput and batched-workload side measurements")
+    ap.add_argument("--aft-table", action="store_true",
+                    help="FFT-stage runtime ratio, plain upsampled FFT / AFT (Table 5.1), then exit")
     ap.add_argument("--profile-only", action="store_true",
                     help="only warm-up + timed steps (for ncu launch lists); prints a short line")
     return ap.parse_args()
@@ -455,6 +457,56 @@ def measure_batched(stream, steps=5):
                         "autotuned at rms 1e-6, one CUDA-graph launch per step"}
 
 
+def smooth_at_least(n):
+    """Smallest 2^a 3^b 5^c 7^d >= n (the plan's FFT sizes)."""
+    while True:
+        m = n
+        for r in (2, 3, 5, 7):
+            while m % r == 0:
+                m //= r
+        if m == 1:
+            return n
+        n += 1
+
+
+def aft_table(args):
+    """Table 5.1: Fourier-stage time of the plain upsampled FFT (every k3 mode padded to s Mt,
+    i.e. s_l = s0 and n_l = k_inf) over the AFT (k3 = 0 and |k3| <= n_l = 8 padded to s Mt, the
+    rest unpadded), for s in {2, 4} and cubic M = 16..128.  P = 16, xi = M/4 (eta = 0.35), N = 1000,
+    no real space; the FFT work does not depend on N or xi.  One JSON line per (s, M)."""
+    import torch
+    from paper_1611_09538_gb300 import build as lib_build
+    from paper_1611_09538_gb300 import inputs, se1p
+    lib_build.build()
+    prec = se1p.SE1P_MIXED if args.precision == "mixed" else se1p.SE1P_FP64
+    x, q = inputs.uniform_alternating(1000, seed=0)
+    xd = torch.as_tensor(x, device="cuda")
+    qd = torch.as_tensor(q, device="cuda")
+    steps = max(args.steps, 10)
+
+    def fourier_ms(M, Mt, ns, nl):
+        plan = se1p.Plan((1.0, 1.0, 1.0), M / 4.0, (M, M, M), 16, len(q), Mt=Mt, n0=ns, nI=ns, nl=nl, rc=0.0,
+                         precision=prec)
+        for _ in range(max(args.warmup, 3)):
+            plan.eval(xd, qd, check=False)
+        se1p.se1p_plan_set_profiling(plan.handle, True)
+        for _ in range(steps):
+            plan.eval(xd, qd, check=False)
+        ms, ne = se1p.se1p_plan_stage_times(plan.handle)
+        plan.close()
+        return ms["fourier"] / ne
+
+    for s in (2, 4):
+        for M in (16, 32, 48, 64, 80, 96, 112, 128):
+            Mt = smooth_at_least(M + 16)
+            ns = smooth_at_least(s * Mt)
+            t_aft = fourier_ms(M, Mt, ns, 8)
+            t_plain = fourier_ms(M, Mt, ns, M // 2)
+            print(json.dumps({"table": "5.1", "s_l": s, "M": M, "Mt": Mt, "ns": ns, "precision": args.precision,
+                              "fourier_ms_aft": t_aft, "fourier_ms_plain": t_plain,
+                              "ratio_plain_over_aft": t_plain / t_aft}), flush=True)
+
+
 # ------------------------------------------------------------------ reference arm (the oracle)
 def oracle_step(sys_, n_sources, seed):
     """One reference step: the direct sums for one target against n_sources of the N sources.
@@ -512,6 +564,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.aft_table:
+        aft_table(args)
     else:
         run_gpu(args, rank, world, local_rank)
 

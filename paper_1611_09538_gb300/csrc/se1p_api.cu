@@ -252,6 +252,8 @@ se1p_status flags_to_status(int f)
 
 bool bad_n(const se1p_plan *p, int n) { return n < 0 || n > p->n_max; }
 
+constexpr double kCellsPerRc = 2.0;  // real-space cells per cutoff length
+
 // The spread grid holds unnormalised windows; this factor turns it into Eq. 3.4's grid.
 double window_norm3(const se1p_plan *p) { return p->geo.wnorm_xy * p->geo.wnorm_xy * p->geo.wnorm_z; }
 
@@ -341,8 +343,8 @@ se1p_status se1p_plan_create(const se1p_params *prm, int n_max, se1p_plan **out)
     g.rc = P.rc > 0.0 ? P.rc : 0.0;
     g.rc2 = g.rc * g.rc;
     if (g.rc > 0.0) {
-        // cells of edge >= rc/2 (stencil of +-2 cells), at most 2^22 cells in total
-        const double ce = g.rc / 2.0;
+        // cells of edge >= rc / kCellsPerRc (stencil of +-kCellsPerRc cells), at most 2^22 cells
+        const double ce = g.rc / kCellsPerRc;
         g.ncx = (int)fmin(fmax(floor(P.L[0] / ce), 1.0), 1024.0);
         g.ncy = (int)fmin(fmax(floor(P.L[1] / ce), 1.0), 1024.0);
         g.ncz = (int)fmin(fmax(floor(P.L[2] / ce), 1.0), 8192.0);

@@ -72,6 +72,8 @@ CASES = {
                               nI=98, nl=2, rc=0.25),
     # C1-like: P = 16, M = 32, Mt = 48
     "c1_like": small_case(n=1000, seed=0, xi=8.0, M=(32, 32, 32), P=16, Mt=48, n0=144, nI=144, nl=3),
+    # plain upsampled FFT (Section 3.2: s_l = s0, n_l = k_inf): every k3 mode padded to nI = n0
+    "plain_upsampled": small_case(n=500, seed=7, xi=8.0, M=(32, 32, 32), P=16, Mt=48, n0=144, nI=144, nl=16),
     # elongated periodic axis: M3 = 256 (K3 = 129 z modes, 32 of them in the set I)
     "elongated": small_case(n=600, L=(1.0, 1.0, 8.0), seed=6, xi=8.0, M=(32, 32, 256), P=16, Mt=48, n0=144,
                             nI=96, nl=4, rc=0.3),
@@ -162,7 +164,7 @@ def test_parity_config_matches_direct_sums():
     assert r.energy.item() == pytest.approx(U_ref, rel=1e-10)
 
 
-@pytest.mark.parametrize("case", ["cubic_P24", "c1_like"])
+@pytest.mark.parametrize("case", ["cubic_P24", "c1_like", "plain_upsampled"])
 def test_mixed_matches_fp64(case):
     x, q, prm = CASES[case]
     p64 = make_plan(prm, len(q))

@@ -13,6 +13,8 @@ namespace {
 constexpr int kRealWarps = 4;  // warps per CTA (warps work independently)
 constexpr int kRealSplit = 4;  // warps sharing one group of 32 targets (source rows split between them)
 constexpr int kCand = 96;      // per-warp candidate list (flushed at >= 64)
+constexpr int kRealTargets = 16;                     // targets per warp
+constexpr int kLanesPerTarget = 32 / kRealTargets;   // lanes sharing a target (alternate candidates)
 
 // Hardware approximations with denormals flushed (arguments here are far from the
 // denormal range: r^2 >= ~1e-14, exp(-xi^2 r^2) >= ~1e-11, 1 + x/2 >= 1).
@@ -119,9 +121,10 @@ __device__ __forceinline__ void pair_terms(T dx, T dy, T dz, T qs, T rc2, T xi, 
     fz += fs * dz;
 }
 
-// Real-space sum, warp-centric.  Warp w owns the 32 consecutive targets
-// 32w..32w+31 in cell order (all lanes busy, any cell boundaries), so its
-// targets occupy a small box of cells.  Sources come from that box expanded by
+// Real-space sum, warp-centric.  Warp w owns the kRealTargets consecutive targets
+// from kRealTargets w in cell order (any cell boundaries), so its targets occupy a
+// small box of cells; kLanesPerTarget lanes share a target and take alternate
+// candidates.  Sources come from that box expanded by
 // S = ceil(rc / cell edge) cells per axis; for each (y, z) cell row the x-range
 // is contiguous in cell order, i.e. one source range; z images come from
 // unwrapped rows nz_u = nz + wrap * ncz, shifted by wrap * L3 (folded into the
@@ -130,8 +133,8 @@ __device__ __forceinline__ void pair_terms(T dx, T dy, T dz, T qs, T rc2, T xi, 
 // Sources are read 32 at a time, one per lane, and tested in parallel against
 // the warp's target bounding box grown by rc; the survivors are compacted by
 // ballot into a per-warp list.  When the list holds >= 64 candidates:
-//   phase 1: every lane marks the candidates within rc of its own target (float
-//            test on the hi parts, threshold widened so no true pair is lost);
+//   phase 1: every lane marks its share of the candidates within rc of its target
+//            (float test on the hi parts, threshold widened so no true pair is lost);
 //   phase 2: every lane walks its own marks: hi + lo displacement, the exact
 //            r <= rc test and the pair terms, branch-free.
 // (Spreading the marks of busy lanes over idle ones through shared memory was
@@ -148,8 +151,9 @@ __global__ void __launch_bounds__(32 * kRealWarps) k_real(Geo g, int n, const in
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * kRealWarps + wib;
     const int warp = gw / kRealSplit, part = gw % kRealSplit;  // target group, share of the source rows
-    const int t = warp * 32 + lane;
-    if (warp * 32 >= n) return;  // whole warp beyond the particles
+    const int half = lane / kRealTargets;  // which share of the candidates this lane takes
+    const int t = warp * kRealTargets + lane % kRealTargets;
+    if (warp * kRealTargets >= n) return;  // whole warp beyond the particles
     const bool valid = t < n;
     PairRec<T> me;
     int orig = -1;
@@ -214,28 +218,30 @@ __global__ void __launch_bounds__(32 * kRealWarps) k_real(Geo g, int n, const in
         // phase 1: candidates within rc of this lane's target (float test, widened threshold)
         unsigned m0 = 0u, m1 = 0u, m2 = 0u;
         if (valid) {
-            const int n0 = min(nc, 32), n1 = min(nc, 64);
-            for (int j = 0; j < n0; ++j) {
-                const float4 c = cp[j * cps];
+            // candidate j = k kLanesPerTarget + half is bit k of this lane's marks
+            const int nk = (nc - half + kLanesPerTarget - 1) / kLanesPerTarget;
+            const int n0 = min(nk, 32), n1 = min(nk, 64);
+            for (int k = 0; k < n0; ++k) {
+                const float4 c = cp[(k * kLanesPerTarget + half) * cps];
                 const float dx = mxf - c.x, dy = myf - c.y, dz = mzf - c.z;
-                if (dx * dx + dy * dy + dz * dz <= rc2wf) m0 |= 1u << j;
+                if (dx * dx + dy * dy + dz * dz <= rc2wf) m0 |= 1u << k;
             }
-            for (int j = 32; j < n1; ++j) {
-                const float4 c = cp[j * cps];
+            for (int k = 32; k < n1; ++k) {
+                const float4 c = cp[(k * kLanesPerTarget + half) * cps];
                 const float dx = mxf - c.x, dy = myf - c.y, dz = mzf - c.z;
-                if (dx * dx + dy * dy + dz * dz <= rc2wf) m1 |= 1u << (j - 32);
+                if (dx * dx + dy * dy + dz * dz <= rc2wf) m1 |= 1u << (k - 32);
             }
-            for (int j = 64; j < nc; ++j) {
-                const float4 c = cp[j * cps];
+            for (int k = 64; k < nk; ++k) {
+                const float4 c = cp[(k * kLanesPerTarget + half) * cps];
                 const float dx = mxf - c.x, dy = myf - c.y, dz = mzf - c.z;
-                if (dx * dx + dy * dy + dz * dz <= rc2wf) m2 |= 1u << (j - 64);
+                if (dx * dx + dy * dy + dz * dz <= rc2wf) m2 |= 1u << (k - 64);
             }
         }
         // phase 2: this lane's marks, word by word
         T pphi = 0, pfx = 0, pfy = 0, pfz = 0;
-        auto walk = [&](unsigned m, int j0) {
+        auto walk = [&](unsigned m, int k0) {
             while (m) {
-                const int j = j0 + __ffs(m) - 1;
+                const int j = (k0 + __ffs(m) - 1) * kLanesPerTarget + half;
                 m &= m - 1u;
                 T dx, dy, dz;
                 displacement(me, cl[j], dx, dy, dz);
@@ -304,7 +310,14 @@ __global__ void __launch_bounds__(32 * kRealWarps) k_real(Geo g, int n, const in
         }
     }
     if (ncand > 0) process(ncand);
-    if (valid) {
+#pragma unroll
+    for (int o = kRealTargets; o < 32; o <<= 1) {  // lanes sharing a target
+        aphi += __shfl_xor_sync(full, aphi, o);
+        afx += __shfl_xor_sync(full, afx, o);
+        afy += __shfl_xor_sync(full, afy, o);
+        afz += __shfl_xor_sync(full, afz, o);
+    }
+    if (valid && half == 0) {
         // the kRealSplit warps of a target group combine through FP64 atomics
         // (outputs are zeroed beforehand when not accumulating)
         const double qm = (accumulate & 2) ? 1.0 : (double)qme;  // bit 1: field instead of force
@@ -327,7 +340,7 @@ void launch_real_space(se1p_plan *p, int n, const int *cell_key, double *phi, do
         cudaMemsetAsync(phi, 0, sizeof(double) * (size_t)n, s);
         cudaMemsetAsync(frc, 0, sizeof(double) * 3 * (size_t)n, s);
     }
-    const int warps = (n + 31) / 32 * kRealSplit;
+    const int warps = (n + kRealTargets - 1) / kRealTargets * kRealSplit;
     k_real<T><<<(warps + kRealWarps - 1) / kRealWarps, 32 * kRealWarps, 0, s>>>(
         g, n, p->b.starts + g.nbins + 1, (const CellRec<T> *)p->b.cells, cell_key, phi, frc, accumulate);
 }

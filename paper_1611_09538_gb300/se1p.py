@@ -287,6 +287,15 @@ class Plan:
         self.handle = se1p_plan_create(self.params, n_max)
         self.n_max = n_max
 
+    @classmethod
+    def from_params(cls, params: se1p_params, n_max):
+        """A plan from a filled se1p_params (e.g. the result of se1p_autotune)."""
+        self = cls.__new__(cls)
+        self.params = params
+        self.handle = se1p_plan_create(params, n_max)
+        self.n_max = n_max
+        return self
+
     @property
     def info(self) -> se1p_plan_info:
         return se1p_plan_info_copy(se1p_plan_get_info(self.handle))

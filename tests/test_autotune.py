@@ -65,3 +65,31 @@ def test_autotune_rejects_bad_requests(bad):
     with pytest.raises(se1p.SE1PError) as ei:
         se1p.se1p_autotune(kw["L"], kw["xi"], kw["Q"], kw["n"], kw["tol"])
     assert ei.value.code == 1
+
+
+def _golden_6_1():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "table_6_1.json")) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("tol", [1e-5, 1e-9])
+def test_table_6_1_parameters(tol):
+    """Section 6, Table 6.1 (xi = 4, N/L^3 = 125): the recipe's M, rc and s_l as printed.
+
+    k_inf is taken at tol/100 (the estimates of Eq. 2.10 undershoot the measured k-space error),
+    so M may exceed the printed grid by the sqrt-log growth of k_inf, at most 15%; rc follows
+    Eq. 2.9 at tol itself (printed 0.781 and 1.08); s_l meets exp(-2 pi s_l) <= tol (Eq. 4.8)
+    and, because tol is absolute and the quadrature error grows with sqrt(Q/V), lies between the
+    printed value and one above it; n_l follows M ~ 10 n_l (Eq. 4.9)."""
+    g = _golden_6_1()["table_6_1"]
+    key = "1e-5" if tol == 1e-5 else "1e-9"
+    for N, L, M5, nl5, M9, nl9 in g["rows"]:
+        M_paper = M5 if tol == 1e-5 else M9
+        p = se1p.se1p_autotune((L, L, L), g["xi"], float(N) / 3.0, N, tol)
+        assert M_paper <= p.M[0] <= 1.15 * M_paper, (N, p.M[0], M_paper)
+        assert abs(p.rc / g["rc"][key] - 1.0) < 0.08, (N, p.rc)
+        assert np.exp(-2.0 * np.pi * p.sl) <= tol * 1.0001
+        assert g["sl"][key] - 0.1 <= p.nI / p.Mt <= g["sl"][key] + 1.0, (N, p.nI / p.Mt)
+        assert p.nl == int(np.ceil(p.M[0] / 10.0))

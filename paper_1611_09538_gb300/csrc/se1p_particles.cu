@@ -708,7 +708,9 @@ void launch_gather(se1p_plan *p, int n, const void *grid, double *phi, double *f
     const bool vec = g.Mt % V == 0;
     if (vec && g.P == 24) k_gather_vec<T, 24><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
     else if (vec && g.P == 16) k_gather_vec<T, 16><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
+    else if (vec && g.P == 12) k_gather_vec<T, 12><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
     else if (g.P == 24) k_gather<T, 24><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
+    else if (g.P == 12) k_gather<T, 12><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
     else if (g.P == 16) k_gather<T, 16><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
     else k_gather<T, 0><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
 }

@@ -8,6 +8,7 @@ Workloads (positions in the box [0,Lx)x[0,Ly)x[0,Lz), z periodic):
   * uniform charges with alternating signs (Section 6, Examples 6.1-6.3),
   * uniform charges with U[-1,1] values shifted to zero net charge,
   * Gaussian blobs (clustered systems, a stress case for cell lists),
+  * a charged wall facing an oppositely charged cloud (stand-in for Example 6.6),
   * batches of independent systems with log-uniform N and random Lz.
 Every generator uses numpy's PCG64 (``default_rng(seed)``) in float64.
 """
@@ -71,6 +72,40 @@ def clustered(n: int, L=(1.0, 1.0, 2.0), centres: int = 8, sigma: float = 0.05,
     x[:, 2] = np.mod(x[:, 2], Lz)
     x[:, 2][x[:, 2] >= Lz] = 0.0
     q = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    if n % 2 == 1:
+        q[-1] = 0.0
+    return x, q
+
+
+def cloud_wall_like(n: int, L: float, seed: int = 5) -> tuple[np.ndarray, np.ndarray]:
+    """A charged wall facing a cloud of opposite charge, in the cube [0,L)^3 (z periodic).
+
+    Stand-in for the cloud-wall system of Section 6 (Example 6.6), whose generator the paper
+    does not give: a strongly polar arrangement with a large dipole along the free axis x.
+    Charges +1 (first half): x ~ L/2 + N(0, (0.01 L)^2), y, z uniform.  Charges -1 (second
+    half): a Gaussian cloud around (L/4, L/2, L/2) with sigma = L/10.  x, y samples outside
+    [0, L) are redrawn; z is wrapped.  Neutral for even n."""
+    rng = np.random.default_rng(seed)
+    n_wall = n - n // 2
+    x = np.empty((n, 3))
+    x[:n_wall, 0] = L / 2 + 0.01 * L * rng.standard_normal(n_wall)
+    x[:n_wall, 1:] = rng.random((n_wall, 2)) * L
+    c = np.array([L / 4, L / 2, L / 2])
+    x[n_wall:] = c + 0.1 * L * rng.standard_normal((n - n_wall, 3))
+    for ax in (0, 1):
+        while True:
+            bad = np.flatnonzero((x[:, ax] < 0) | (x[:, ax] >= L))
+            if bad.size == 0:
+                break
+            wall, cloud = bad[bad < n_wall], bad[bad >= n_wall]
+            if ax == 0:
+                x[wall, 0] = L / 2 + 0.01 * L * rng.standard_normal(wall.size)
+            else:
+                x[wall, 1] = rng.random(wall.size) * L
+            x[cloud, ax] = c[ax] + 0.1 * L * rng.standard_normal(cloud.size)
+    x[:, 2] = np.mod(x[:, 2], L)
+    x[:, 2][x[:, 2] >= L] = 0.0
+    q = np.where(np.arange(n) < n_wall, 1.0, -1.0)
     if n % 2 == 1:
         q[-1] = 0.0
     return x, q

@@ -1,0 +1,70 @@
+"""The cloud-wall stand-in (Section 6, Example 6.6 and Table 6.2; the paper does not give the
+generator, see inputs.cloud_wall_like) on the N = 19 200 row: L = 40, M = 64, n_l = 4, s_l = 2,
+P = 12, xi = 0.7186, s0 = 2.4, rc = 5.
+
+A charged wall and an opposite cloud give a large dipole along a free axis, the case the
+Vico-truncated k3 = 0 mode and the upsampling must handle.  At 24 sampled targets:
+  * parity: FP64 phi and F equal the restatement of Algorithm 1 (k-space) plus the direct
+    real-space and self terms, element by element (1e-10 of the largest value);
+  * accuracy of the method at these shapes: the k-space force (GPU total minus GPU real space)
+    against the direct Ewald1P k-space sums.  The restatement itself gives 1.0e-4 rms here
+    (Table 6.2 prints 1.7e-5 for its own, unpublished, cloud-wall system), bound 2e-4;
+  * mixed FP32/FP64 against FP64: relative rms <= 1e-6 for phi and F."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import direct  # noqa: E402
+from oracle import se1p_algorithm as se  # noqa: E402
+from paper_1611_09538_gb300 import build as se1p_build  # noqa: E402
+from paper_1611_09538_gb300 import inputs, se1p  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    se1p_build.build()
+    se1p.load()
+    direct.build()
+
+
+def rel(a, b):
+    return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2)))
+
+
+def test_cloud_wall_row_19200():
+    N, L, M, nl, xi, P, rc = 19200, 40.0, 64, 4, 0.7186, 12, 5.0
+    Mt, n0, nI = 80, 192, 160
+    x, q = inputs.cloud_wall_like(N, L)
+    xd, qd = torch.as_tensor(x, device="cuda"), torch.as_tensor(q, device="cuda")
+    out = {}
+    for prec in (se1p.SE1P_FP64, se1p.SE1P_MIXED):
+        plan = se1p.Plan((L, L, L), xi, (M, M, M), P, N, Mt=Mt, n0=n0, nI=nI, nl=nl, rc=rc, precision=prec)
+        r = plan.eval(xd, qd)
+        pr = torch.zeros(N, dtype=torch.float64, device="cuda")
+        fr = torch.zeros((N, 3), dtype=torch.float64, device="cuda")
+        se1p.se1p_real_space(plan.handle, N, xd, qd, pr, fr)
+        torch.cuda.synchronize()
+        out[prec] = (r.phi.cpu().numpy(), r.force.cpu().numpy(), fr.cpu().numpy())
+        plan.close()
+    phi, F, Freal = out[se1p.SE1P_FP64]
+    tg = np.random.default_rng(9).choice(N, size=24, replace=False)
+    # parity with Algorithm 1 + the direct real space and self term
+    phiF, FF = se.se1p_fourier(x, q, (L, L, L), xi, (M, M, M), P, Mt, n0, nI, nl, targets=tg)
+    pp, ff = direct.ewald1p_parts(x, q, L, xi, rc, targets=tg, kcut=1e300)
+    phi_ref, F_ref = phiF + pp[:, 0] + pp[:, 3], FF + ff[:, 0]
+    assert np.max(np.abs(phi[tg] - phi_ref)) < 1e-10 * np.max(np.abs(phi_ref))
+    assert np.max(np.abs(F[tg] - F_ref)) < 1e-10 * np.max(np.abs(F_ref))
+    # the method's k-space error at these shapes
+    pk, fk = direct.ewald1p_parts(x, q, L, xi, -1.0, targets=tg)
+    Fk = F[tg] - Freal[tg]
+    kerr = np.sqrt(np.mean(np.sum((Fk - (fk[:, 1] + fk[:, 2])) ** 2, axis=1)))
+    print(f"cloud-wall N={N}: k-space rms force error {kerr:.2e}; mixed vs FP64 phi "
+          f"{rel(out[1][0], phi):.2e}, F {rel(out[1][1], F):.2e}")
+    assert kerr < 2e-4
+    assert rel(out[se1p.SE1P_MIXED][0], phi) < 1e-6
+    assert rel(out[se1p.SE1P_MIXED][1], F) < 1e-6

@@ -241,6 +241,22 @@ def kernels_per_eval(info, real_space):
     return 4 + 1 + 3 * classes + 1 + 1 + (1 if real_space else 0) + 2
 
 
+# ------------------------------------------------------------------ multi-rank bookkeeping
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The job's figure for a per-rank time: the maximum over ranks (the slowest replica)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args, rank, world, local_rank):
     import torch
@@ -330,10 +346,7 @@ def run_gpu(args, rank, world, local_rank):
     st = se1p.se1p_plan_sync_status(plan.handle, stream)
     if st != 0:
         raise RuntimeError(f"device status {se1p.STATUS.get(st)}")
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
 
     # end to end through the host entry point: pinned host buffers, H2D + eval + D2H each step
     xh = torch.as_tensor(sys_.x).contiguous().pin_memory()
@@ -350,10 +363,7 @@ def run_gpu(args, rank, world, local_rank):
     for _ in range(e2e_steps):
         se1p.se1p_eval_host(plan.handle, n, xh.numpy(), qh.numpy(), phih.numpy(), Fh.numpy(), Eh.numpy(), stream)
     e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = t.item()
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
 
     if rank != 0:
         if dist is not None:
@@ -362,7 +372,7 @@ def run_gpu(args, rank, world, local_rank):
 
     peaks, peak_src = read_peaks()
     ms_per_step = total_ms / args.steps
-    value = world * n * args.steps / (total_ms * 1e-3)
+    value = job_rate(n * args.steps, world, total_ms * 1e-3)
     rf = roofline(stage_ms, n_evals, info, n, args.precision, peaks, clocks and clocks["sm_mhz"], args.workload)
     rf["peak_source"] = ("derived: 152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz" if rf["bound"] == "alu"
                          else f"{peak_src} hbm_gbs")
@@ -377,7 +387,7 @@ def run_gpu(args, rank, world, local_rank):
         "roofline": {k: rf[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")},
         "roofline_detail": {"kernel": rf["kernel"], "algorithmic": rf["algorithmic"],
                             "peak_source": rf["peak_source"], "stage_ms_per_step": rf["stage_ms"]},
-        "e2e": {"value": world * n * e2e_steps / e2e_s, "unit": UNIT,
+        "e2e": {"value": job_rate(n * e2e_steps, world, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": int(n * 4 * 8), "d2h_bytes_per_step": int(n * 4 * 8 + 8)},
         "gpu_launches": int(launches_per_eval * args.steps),
         "clocks": clocks,

@@ -184,62 +184,84 @@ __device__ __forceinline__ float exp_window(float x)
     return p * __int_as_float(((int)n + 127) << 23);
 }
 
-// Scatter into bin order (with the window tables) and into cell order.
+// Scatter into bin order (with the window tables) and into cell order.  One thread per
+// particle computes its window values into a per-warp shared buffer (row stride 3P + 1, so the
+// lanes' rows start in different banks); the warp then writes each particle's row of 3P values
+// to the table with consecutive lanes on consecutive elements.
+constexpr int kScatterThreads = 64;  // FP64 launches half of it: its buffer stays below 48 KB
+
 template <typename T>
-__global__ void k_scatter(Geo g, int n, const double *__restrict__ xyzq, const int *__restrict__ bin_key,
-                          const int *__restrict__ cell_key, int *__restrict__ bin_cursor,
-                          int *__restrict__ cell_cursor, PartRec<T> *__restrict__ parts, T *__restrict__ wts,
-                          CellRec<T> *__restrict__ cells)
+__global__ void __launch_bounds__(kScatterThreads) k_scatter(Geo g, int n, const double *__restrict__ xyzq,
+                                                             const int *__restrict__ bin_key,
+                                                             const int *__restrict__ cell_key,
+                                                             int *__restrict__ bin_cursor,
+                                                             int *__restrict__ cell_cursor,
+                                                             PartRec<T> *__restrict__ parts,
+                                                             T *__restrict__ wts, CellRec<T> *__restrict__ cells)
 {
+    extern __shared__ __align__(16) unsigned char scatter_raw[];
+    const int rowlen = 3 * g.P, rs = rowlen + 1;
+    const int lane = threadIdx.x & 31;
+    T *stage = reinterpret_cast<T *>(scatter_raw) + (threadIdx.x >> 5) * 32 * rs;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double4 p = reinterpret_cast<const double4 *>(xyzq)[i];
-    const Support s = particle_support(g, p.x, p.y, p.z);
-    const int pos = atomicAdd(bin_cursor + bin_key[i], 1);
-    PartRec<T> r;
-    r.i0[0] = s.i0[0];
-    r.i0[1] = s.i0[1];
-    r.i0[2] = imod(s.i0[2], g.M3);
-    r.orig = i;
-    r.q = (T)p.w;
-    T *w = wts + (size_t)pos * 3 * g.P;
-    // Unnormalised windows exp(-alpha d^2): the normalisation (2 xi^2 / (pi eta))^{1/2}
-    // per axis is applied once, in FP64, after the gather, so that no rounded constant
-    // biases the FP32 grid (a bias there would not cancel against the self term).
-    for (int a = 0; a < 3; ++a) {
-        const double gg = s.t[a] - s.i0[a] - g.c;  // particle offset from the support centre, grid units
-        r.g[a] = (T)gg;
-        const double alpha = a < 2 ? g.alpha_xy : g.alpha_z;
-        if constexpr (sizeof(T) == sizeof(double)) {
-            for (int j = 0; j < g.P; ++j) {
-                const double d = gg - (double)(j - g.c);
-                w[a * g.P + j] = exp(-alpha * d * d);
-            }
-        } else {
-            // FP32 window: |gg| < 1, so gg - (j - c) is exact to ~6e-8 absolute; alpha is
-            // split into hi + lo so that its rounding does not bias every exponent alike
-            const float gf = (float)gg, ah = (float)alpha, al = (float)(alpha - (double)ah);
-            for (int j = 0; j < g.P; ++j) {
-                const float d = gf - (float)(j - g.c);
-                const float d2 = d * d;
-                w[a * g.P + j] = exp_window(-fmaf(ah, d2, al * d2));
+    int pos = -1;
+    if (i < n) {
+        const double4 p = reinterpret_cast<const double4 *>(xyzq)[i];
+        const Support s = particle_support(g, p.x, p.y, p.z);
+        pos = atomicAdd(bin_cursor + bin_key[i], 1);
+        PartRec<T> r;
+        r.i0[0] = s.i0[0];
+        r.i0[1] = s.i0[1];
+        r.i0[2] = imod(s.i0[2], g.M3);
+        r.orig = i;
+        r.q = (T)p.w;
+        T *w = stage + lane * rs;
+        // Unnormalised windows exp(-alpha d^2): the normalisation (2 xi^2 / (pi eta))^{1/2}
+        // per axis is applied once, in FP64, after the gather, so that no rounded constant
+        // biases the FP32 grid (a bias there would not cancel against the self term).
+        for (int a = 0; a < 3; ++a) {
+            const double gg = s.t[a] - s.i0[a] - g.c;  // particle offset from the support centre, grid units
+            r.g[a] = (T)gg;
+            const double alpha = a < 2 ? g.alpha_xy : g.alpha_z;
+            if constexpr (sizeof(T) == sizeof(double)) {
+                for (int j = 0; j < g.P; ++j) {
+                    const double d = gg - (double)(j - g.c);
+                    w[a * g.P + j] = exp(-alpha * d * d);
+                }
+            } else {
+                // FP32 window: |gg| < 1, so gg - (j - c) is exact to ~6e-8 absolute; alpha is
+                // split into hi + lo so that its rounding does not bias every exponent alike
+                const float gf = (float)gg, ah = (float)alpha, al = (float)(alpha - (double)ah);
+                for (int j = 0; j < g.P; ++j) {
+                    const float d = gf - (float)(j - g.c);
+                    const float d2 = d * d;
+                    w[a * g.P + j] = exp_window(-fmaf(ah, d2, al * d2));
+                }
             }
         }
+        parts[pos] = r;
+        // cell order, absolute coordinates as hi + lo
+        const int cell = cell_key[i];
+        const int cpos = atomicAdd(cell_cursor + cell, 1);
+        CellRec<T> c;
+        c.xh = (T)p.x;
+        c.yh = (T)p.y;
+        c.zh = (T)p.z;
+        c.xl = (T)(p.x - (double)c.xh);
+        c.yl = (T)(p.y - (double)c.yh);
+        c.zl = (T)(p.z - (double)c.zh);
+        c.q = (T)p.w;
+        c.orig = i;
+        cells[cpos] = c;
     }
-    parts[pos] = r;
-    // cell order, absolute coordinates as hi + lo
-    const int cell = cell_key[i];
-    const int cpos = atomicAdd(cell_cursor + cell, 1);
-    CellRec<T> c;
-    c.xh = (T)p.x;
-    c.yh = (T)p.y;
-    c.zh = (T)p.z;
-    c.xl = (T)(p.x - (double)c.xh);
-    c.yl = (T)(p.y - (double)c.yh);
-    c.zl = (T)(p.z - (double)c.zh);
-    c.q = (T)p.w;
-    c.orig = i;
-    cells[cpos] = c;
+    __syncwarp();
+    for (int k = 0; k < 32; ++k) {
+        const int pk = __shfl_sync(0xffffffffu, pos, k);
+        if (pk < 0) continue;  // warp-uniform
+        T *dst = wts + (size_t)pk * rowlen;
+        const T *src = stage + k * rs;
+        for (int e = lane; e < rowlen; e += 32) dst[e] = src[e];
+    }
 }
 
 // ------------------------------------------------------------------ gridding (Eq. 3.4)
@@ -667,7 +689,11 @@ template <typename T> void launch_sort_scatter(se1p_plan *p, int n, cudaStream_t
 {
     const Geo &g = p->geo;
     if (n <= 0) return;
-    k_scatter<T><<<blocks_for(n, 128), 128, 0, s>>>(g, n, p->b.xyzq, p->b.bin_key, p->b.cell_key,
+    // one thread per particle (no grid-stride loop, so no cap on the CTA count); per-warp buffers of
+    // 32 rows of 3P + 1 values: at most 24.8 KB per CTA (P <= 32)
+    const int nt = sizeof(T) == sizeof(float) ? kScatterThreads : kScatterThreads / 2;
+    const size_t sm = sizeof(T) * (size_t)nt * (3 * g.P + 1);
+    k_scatter<T><<<blocks_for(n, nt, 0x7fffffff), nt, sm, s>>>(g, n, p->b.xyzq, p->b.bin_key, p->b.cell_key,
                                                       p->b.cursors, p->b.cursors + g.nbins,
                                                       (PartRec<T> *)p->b.parts, (T *)p->b.wts,
                                                       (CellRec<T> *)p->b.cells);

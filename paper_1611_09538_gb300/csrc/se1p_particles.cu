@@ -661,6 +661,8 @@ __global__ void k_convert(size_t n, const TS *__restrict__ src, TD *__restrict__
         dst[i] = (TD)((double)src[i] * scale);
 }
 
+// CTAs for n items of bs threads; kernels with one thread per item and no grid-stride loop
+// pass an uncapped limit
 inline int blocks_for(size_t n, int bs, int cap = 1 << 20)
 {
     size_t b = (n + bs - 1) / bs;
@@ -678,7 +680,7 @@ void launch_pack(se1p_plan *p, int n, const double *x, const double *q, cudaStre
     cudaMemsetAsync(p->b.counts, 0, sizeof(int) * (g.nbins + g.ncells), s);
     cudaMemsetAsync(p->b.sums, 0, sizeof(double) * 2, s);
     if (n > 0)
-        k_pack<T><<<blocks_for(n, 256), 256, 0, s>>>(g, n, x, q, p->b.xyzq, p->b.bin_key, p->b.cell_key,
+        k_pack<T><<<blocks_for(n, 256, 0x7fffffff), 256, 0, s>>>(g, n, x, q, p->b.xyzq, p->b.bin_key, p->b.cell_key,
                                                        p->b.counts, p->b.counts + g.nbins, p->b.sums,
                                                        p->b.status);
     k_scan<<<2, 1024, 0, s>>>(g.nbins, g.ncells, p->b.counts, p->b.starts, p->b.cursors, p->b.sums,
@@ -744,7 +746,7 @@ void launch_gather(se1p_plan *p, int n, const void *grid, double *phi, double *f
 void launch_vjp_combine(int n, const double *q, const double *v, const double *Eq, const double *phiv,
                         const double *Ev, double *grad_x, double *grad_q, cudaStream_t s)
 {
-    if (n > 0) k_vjp_combine<<<blocks_for(n, 256), 256, 0, s>>>(n, q, v, Eq, phiv, Ev, grad_x, grad_q);
+    if (n > 0) k_vjp_combine<<<blocks_for(n, 256, 0x7fffffff), 256, 0, s>>>(n, q, v, Eq, phiv, Ev, grad_x, grad_q);
 }
 
 void launch_finalize(se1p_plan *p, int n, double *phi, double *frc, double *energy, cudaStream_t s)

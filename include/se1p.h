@@ -206,9 +206,9 @@ typedef struct {
  *   (scaled by the axis length; even 2^a 3^b 5^c 7^d sizes), P from Eq. 4.3 (even,
  *   at most 32); k_inf and P are taken for tol/100 (the printed estimates undershoot
  *   the measured k-space error by 5-20x), s_l at the lowest mode k3 = 2 pi/L3 from
- *   250 sqrt(Q/V) exp(-|k3| s_l Mt h) <= tol (the trapezoidal rule's error of Section 4.2, whose
- *   amplitude grows with the charge content) and at least exp(-|k3| s_l L) <= tol (Eq. 4.8 when
- *   L3 = L), n_l = ceil(M/10) (Eq. 4.9), s0 = 2 sqrt 2;
+ *   sqrt(Q/V) exp(-|k3| (s_l Mt h - L)) <= tol (the trapezoidal rule's error of Section 4.2: its
+ *   nearest implied images lie s_l Mt h - L away, its amplitude grows with the charge content) and
+ *   at least exp(-|k3| s_l L) <= tol (Eq. 4.8 when L3 = L), n_l = ceil(M/10) (Eq. 4.9), s0 = 2 sqrt 2;
  *   Mt, n0, nI are then fixed to smooth sizes.  Host only, no GPU work.
  *   SE1P_ERR_INVALID_ARG for non-positive lengths, xi, Q, n or tol outside (0,1). */
 se1p_status se1p_autotune(const se1p_tune_request *req, se1p_params *out);

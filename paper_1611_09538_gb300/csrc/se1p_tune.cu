@@ -28,8 +28,6 @@ constexpr double kC = 0.95;
 // (checked against the direct sums); k_inf and P are therefore chosen for tol/100.
 // The real-space estimate (Eqs. 2.7/2.9) is used as printed.
 constexpr double kKspaceSafety = 100.0;
-// bound on the amplitude of the lowest mode's quadrature error in units of sqrt(Q / V)
-constexpr double kQuadAmplitude = 250.0;
 
 // Principal branch of Lambert W for x >= 0 (w e^w = x), Halley's iteration.
 double lambert_w(double x)
@@ -135,15 +133,16 @@ se1p_status se1p_autotune(const se1p_tune_request *req, se1p_params *out)
     const double h = req->L[0] / M[0];
     p.Mt = next_smooth_any(M[0] + P);
     p.n0 = next_smooth_any((long)ceil(2.0 * sqrt(2.0) * p.Mt - 1e-9));
-    // Section 4.2: the lowest mode k3 = 2 pi / L3 is integrated by the trapezoidal rule over
-    // the period s_l Lt (Lt = Mt h), with an error A exp(-|k3| s_l Lt).  Eq. 4.8 bounds that
-    // error relative to the mode; tol is absolute, and A grows with the charge content: on the
-    // restatement of Algorithm 1 (cubic boxes, L = 1..10, Q = 1..7e3, xi = 3..20) A / sqrt(Q/V)
-    // stayed below kQuadAmplitude.  Hence A exp(-|k3| s_l Lt) <= tol with that bound, and at
-    // least Eq. 4.8 itself (exp(-|k3| s_l L) <= tol).
+    // Section 4.2: the lowest mode k3 = 2 pi / L3 is integrated by the trapezoidal rule over the
+    // period s_l Lt (Lt = Mt h).  Its error is that of the periodic images the rule implies: the
+    // nearest lie s_l Lt - L away, so it behaves like A exp(-|k3| (s_l Lt - L)).  Eq. 4.8 bounds the
+    // error relative to the mode; tol is absolute and A grows with the charge content: on the
+    // restatement of Algorithm 1 (L = 1..10, L3 / L = 1..3, Q = 1..7e3, xi = 3..20) A / sqrt(Q/V)
+    // stayed in 0.2..0.6.  Hence sqrt(Q/V) exp(-|k3| (s_l Lt - L)) <= tol, and at least Eq. 4.8
+    // itself (exp(-|k3| s_l L) <= tol).
     const double k3min = 2.0 * kPiT / req->L[2];
     const double Lt = p.Mt * h;
-    double sl = fmax(log(kQuadAmplitude * sqrt(Q / V) / eps) / (k3min * Lt), log(1.0 / eps) / (k3min * req->L[0]));
+    double sl = fmax((log(sqrt(Q / V) / eps) + k3min * req->L[0]) / (k3min * Lt), log(1.0 / eps) / (k3min * req->L[0]));
     if (sl < 1.0) sl = 1.0;
     p.nI = next_smooth_any((long)ceil(sl * p.Mt - 1e-9));
     // Eq. 4.9: M ~ 10 n_l (free-axis units)

@@ -50,10 +50,13 @@ def test_table_4_1_grid_sizes_at_moderate_accuracy():
 
 
 def test_elongated_box_upsamples_low_modes():
-    """The lowest z mode of a long box (k3 = 2 pi / L3) needs s_l ~ ln(1/tol) L3 / (2 pi L)."""
+    """The lowest z mode of a long box (k3 = 2 pi / L3) is integrated with an error that decays
+    like exp(-|k3| (s_l Lt - L)) (the nearest images implied by the rule lie s_l Lt - L away,
+    Section 4.2), so the upsampled length beyond the box, s_l Lt - L, grows in proportion to L3."""
     p1 = se1p.se1p_autotune((1.0, 1.0, 1.0), 20.0, 1e4, 10000, 1e-6)
     p4 = se1p.se1p_autotune((1.0, 1.0, 4.0), 20.0, 1e4, 10000, 1e-6)
-    assert p4.sl > 3.5 * p1.sl
+    beyond = lambda p: p.nI / p.M[0] - 1.0  # s_l Lt - L with Lt = Mt h, h = 1 / M
+    assert 3.5 < beyond(p4) / beyond(p1) < 4.5
     assert p4.M[2] > 3.5 * p1.M[2] and p4.M[0] == p1.M[0]
 
 

@@ -1,6 +1,8 @@
 """Parameters from se1p_autotune (Section 4.3) reach the requested accuracy on the systems of
 Section 6: the first row of Table 6.1 (N = 20 000, L = 5.43, xi = 4, tolerances 1e-5 and 1e-9)
-and of Example 6.1 (N = 21 600, L = 6, xi = 3.5, relative rms error 2e-6).
+and of Example 6.1 (N = 21 600, L = 6, xi = 3.5, relative rms error 2e-6); and an elongated box
+(N = 20 000 in L = [1, 1, 3], xi = 20, 1e-6), where the upsampling of the lowest mode is set by
+the images' distance s_l Lt - L (Section 4.2).
 
 Reference: the direct Ewald1P sums with a converged real space (xi rc = 6.5), at 24 sampled
 targets against all sources.  The autotuner takes rc from Eq. 2.9 at the tolerance itself and
@@ -29,22 +31,23 @@ def _lib():
 
 
 CASES = {
-    "table6.1_tol1e-5_mixed": (20000, 5.43, 4.0, 1e-5, se1p.SE1P_MIXED),
-    "table6.1_tol1e-9_fp64": (20000, 5.43, 4.0, 1e-9, se1p.SE1P_FP64),
-    "example6.1_tol2e-6_mixed": (21600, 6.0, 3.5, 2e-6, se1p.SE1P_MIXED),
+    "table6.1_tol1e-5_mixed": (20000, (5.43,) * 3, 4.0, 1e-5, se1p.SE1P_MIXED),
+    "table6.1_tol1e-9_fp64": (20000, (5.43,) * 3, 4.0, 1e-9, se1p.SE1P_FP64),
+    "example6.1_tol2e-6_mixed": (21600, (6.0,) * 3, 3.5, 2e-6, se1p.SE1P_MIXED),
+    "elongated_L3_3_tol1e-6_fp64": (20000, (1.0, 1.0, 3.0), 20.0, 1e-6, se1p.SE1P_FP64),
 }
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_autotuned_accuracy(case):
     N, L, xi, tol, prec = CASES[case]
-    x, q = inputs.uniform_shifted(N, (L, L, L), seed=61)
-    p = se1p.se1p_autotune((L, L, L), xi, float(np.sum(q * q)), N, tol, prec)
+    x, q = inputs.uniform_shifted(N, L, seed=61)
+    p = se1p.se1p_autotune(L, xi, float(np.sum(q * q)), N, tol, prec)
     plan = se1p.Plan.from_params(p, N)
     r = plan.eval(torch.as_tensor(x, device="cuda"), torch.as_tensor(q, device="cuda"))
     phi = r.phi.cpu().numpy()
     tg = np.random.default_rng(7).choice(N, size=24, replace=False)
-    phi_ref, F_ref, _ = direct.ewald1p(x, q, L, xi, 6.5 / xi, targets=tg)
+    phi_ref, F_ref, _ = direct.ewald1p(x, q, L[2], xi, 6.5 / xi, targets=tg)
     err = np.sqrt(np.mean((phi[tg] - phi_ref) ** 2))
     rel = err / np.sqrt(np.mean(phi_ref ** 2))
     print(f"{case}: M={p.M[0]} P={p.P} rc={p.rc:.3f} nl={p.nl} nI={p.nI} Mt={p.Mt}: "

@@ -82,6 +82,11 @@ void free_all(se1p_plan *p)
 {
     for (void *ptr : p->dev_allocs) cudaFree(ptr);
     p->dev_allocs.clear();
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
+    if (p->s_real) cudaStreamDestroy(p->s_real);
+    p->ev_fork = p->ev_join = nullptr;
+    p->s_real = nullptr;
 }
 
 template <typename T> void upload(void *dst, const std::vector<T> &v)
@@ -174,16 +179,19 @@ se1p_status check_launch()
 
 // ---------------------------------------------------------------- orchestration
 constexpr int kProfMaxEvals = 4096;
-constexpr int kProfEventsPerEval = SE1P_NUM_STAGES + 1;
+constexpr int kProfEventsPerEval = 2 * SE1P_NUM_STAGES;
 
+// Start and end events of each stage of one evaluation, recorded on the stream the stage runs on
+// (the real space overlaps the grid path, so stage times may add up to more than the evaluation).
 struct StageMarks {
     se1p_plan *p;
-    cudaStream_t s;
     bool on;
-    StageMarks(se1p_plan *p_, cudaStream_t s_) : p(p_), s(s_), on(p_->profiling && p_->prof_count < kProfMaxEvals) {}
-    void mark(int boundary)
+    explicit StageMarks(se1p_plan *p_) : p(p_), on(p_->profiling && p_->prof_count < kProfMaxEvals) {}
+    void begin(int stage, cudaStream_t s) { record(2 * stage, s); }
+    void end(int stage, cudaStream_t s) { record(2 * stage + 1, s); }
+    void record(int k, cudaStream_t s)
     {
-        if (on) cudaEventRecord(p->prof_events[(size_t)p->prof_count * kProfEventsPerEval + boundary], s);
+        if (on) cudaEventRecord(p->prof_events[(size_t)p->prof_count * kProfEventsPerEval + k], s);
     }
     void done()
     {
@@ -192,33 +200,59 @@ struct StageMarks {
 };
 
 // One evaluation of phi (with the self term) and of the force (field = 0) or the
-// field -grad phi (field = 1) for charges q at positions x, into phi / frc.
+// field -grad phi (field = 1) for charges q at positions x, into phi / frc.  With phi_r / frc_r
+// the real space runs on the plan's second stream, concurrently with gridding, the Fourier
+// passes and gathering (it needs only the cell-sorted records), and writes there; the caller
+// adds them after this returns (s has waited for them).  Without, it adds into phi / frc on s.
 template <typename T>
 void run_pass(se1p_plan *p, int n, const double *x, const double *q, double *phi, double *frc, int field,
-              int check_neutral, cudaStream_t s, StageMarks *m)
+              int check_neutral, cudaStream_t s, StageMarks *m, double *phi_r = nullptr, double *frc_r = nullptr)
 {
-    if (m) m->mark(SE1P_STAGE_PACK);
+    const int fl = field ? 2 : 0;
+    if (m) m->begin(SE1P_STAGE_PACK, s);
     launch_pack<T>(p, n, x, q, s, check_neutral);
     launch_sort_scatter<T>(p, n, s);
-    if (m) m->mark(SE1P_STAGE_SPREAD);
+    if (m) m->end(SE1P_STAGE_PACK, s);
+    const bool real = p->geo.rc > 0;
+    const bool side = real && phi_r && frc_r;
+    if (side) {
+        cudaEventRecord(p->ev_fork, s);
+        cudaStreamWaitEvent(p->s_real, p->ev_fork, 0);
+        if (m) m->begin(SE1P_STAGE_REAL, p->s_real);
+        launch_real_space<T>(p, n, p->b.cell_key, phi_r, frc_r, fl, p->s_real);
+        if (m) m->end(SE1P_STAGE_REAL, p->s_real);
+        cudaEventRecord(p->ev_join, p->s_real);
+    }
+    if (m) m->begin(SE1P_STAGE_SPREAD, s);
     launch_spread<T>(p, s);
-    if (m) m->mark(SE1P_STAGE_FOURIER);
+    if (m) m->end(SE1P_STAGE_SPREAD, s);
+    if (m) m->begin(SE1P_STAGE_FOURIER, s);
     launch_fourier<T>(p, s);
-    if (m) m->mark(SE1P_STAGE_GATHER);
-    launch_gather<T>(p, n, p->b.grid, phi, frc, 1 | (field ? 2 : 0) | 4, s);
-    if (m) m->mark(SE1P_STAGE_REAL);
-    if (p->geo.rc > 0) launch_real_space<T>(p, n, p->b.cell_key, phi, frc, 1 | (field ? 2 : 0), s);
+    if (m) m->end(SE1P_STAGE_FOURIER, s);
+    if (m) m->begin(SE1P_STAGE_GATHER, s);
+    launch_gather<T>(p, n, p->b.grid, phi, frc, 1 | fl | 4, s);
+    if (m) m->end(SE1P_STAGE_GATHER, s);
+    if (side) {
+        cudaStreamWaitEvent(s, p->ev_join, 0);
+    } else {
+        if (m) m->begin(SE1P_STAGE_REAL, s);
+        if (real) launch_real_space<T>(p, n, p->b.cell_key, phi, frc, 1 | fl, s);
+        if (m) m->end(SE1P_STAGE_REAL, s);
+    }
 }
 
 template <typename T>
 se1p_status run_eval(se1p_plan *p, int n, const double *x, const double *q, double *phi, double *frc,
                      double *energy, cudaStream_t s)
 {
-    StageMarks m(p, s);
-    run_pass<T>(p, n, x, q, p->b.phi_int, p->b.frc_int, 0, 1, s, &m);
-    m.mark(SE1P_STAGE_FINAL);
-    launch_finalize(p, n, phi, frc, energy, s);
-    m.mark(SE1P_NUM_STAGES);
+    StageMarks m(p);
+    // the real space writes phi2 / frc2 (free outside the adjoint) and the finalisation adds them
+    const bool real = p->geo.rc > 0;
+    run_pass<T>(p, n, x, q, p->b.phi_int, p->b.frc_int, 0, 1, s, &m, real ? p->b.phi2 : nullptr,
+                real ? p->b.frc2 : nullptr);
+    m.begin(SE1P_STAGE_FINAL, s);
+    launch_finalize(p, n, phi, frc, energy, s, real ? p->b.phi2 : nullptr, real ? p->b.frc2 : nullptr);
+    m.end(SE1P_STAGE_FINAL, s);
     m.done();
     return check_launch();
 }
@@ -400,6 +434,14 @@ se1p_status se1p_plan_create(const se1p_params *prm, int n_max, se1p_plan **out)
     if (st != SE1P_OK) { free_all(p); delete p; return st; }
     int cfg = mixed ? configure_fourier_kernels<float>(p) : configure_fourier_kernels<double>(p);
     if (cfg != 0) { cudaGetLastError(); free_all(p); delete p; return SE1P_ERR_CUDA; }
+    if (cudaStreamCreateWithFlags(&p->s_real, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        free_all(p);
+        delete p;
+        return SE1P_ERR_CUDA;
+    }
     launch_vico_table(p, 0);
     if (mixed) launch_symbol_tables<float>(p, 0);
     else launch_symbol_tables<double>(p, 0);
@@ -487,8 +529,8 @@ se1p_status se1p_plan_stage_times(se1p_plan *p, double *ms, int *n_evals)
     for (int e = 0; e < p->prof_count; ++e) {
         for (int st = 0; st < SE1P_NUM_STAGES; ++st) {
             float t = 0.f;
-            cudaEvent_t a = p->prof_events[(size_t)e * kProfEventsPerEval + st];
-            cudaEvent_t b = p->prof_events[(size_t)e * kProfEventsPerEval + st + 1];
+            cudaEvent_t a = p->prof_events[(size_t)e * kProfEventsPerEval + 2 * st];
+            cudaEvent_t b = p->prof_events[(size_t)e * kProfEventsPerEval + 2 * st + 1];
             if (cudaEventElapsedTime(&t, a, b) != cudaSuccess) return SE1P_ERR_CUDA;
             ms[st] += t;
         }

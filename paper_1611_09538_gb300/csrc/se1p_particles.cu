@@ -597,19 +597,29 @@ __global__ void __launch_bounds__(256) k_gather_vec(Geo g, int n, const PartRec<
 }
 
 // ------------------------------------------------------------------ outputs and energy
+// phi, F in caller order (the grid path's, plus the real space's when it ran on its own stream)
+// and the per-block partial energies.
 __global__ void k_finalize(int n, const double *__restrict__ xyzq, const double *__restrict__ phi_int,
-                           const double *__restrict__ frc_int, double *__restrict__ phi,
+                           const double *__restrict__ frc_int, const double *__restrict__ phi_add,
+                           const double *__restrict__ frc_add, double *__restrict__ phi,
                            double *__restrict__ frc, double *__restrict__ epart)
 {
     double e = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double ph = phi_int[i];
+        double ph = phi_int[i];
+        if (phi_add) ph += phi_add[i];
         e += xyzq[4 * i + 3] * ph;
         if (phi) phi[i] = ph;
         if (frc) {
-            frc[3 * i] = frc_int[3 * i];
-            frc[3 * i + 1] = frc_int[3 * i + 1];
-            frc[3 * i + 2] = frc_int[3 * i + 2];
+            double f0 = frc_int[3 * i], f1 = frc_int[3 * i + 1], f2 = frc_int[3 * i + 2];
+            if (frc_add) {
+                f0 += frc_add[3 * i];
+                f1 += frc_add[3 * i + 1];
+                f2 += frc_add[3 * i + 2];
+            }
+            frc[3 * i] = f0;
+            frc[3 * i + 1] = f1;
+            frc[3 * i + 2] = f2;
         }
     }
     __shared__ double ws[32];
@@ -749,9 +759,11 @@ void launch_vjp_combine(int n, const double *q, const double *v, const double *E
     if (n > 0) k_vjp_combine<<<blocks_for(n, 256, 0x7fffffff), 256, 0, s>>>(n, q, v, Eq, phiv, Ev, grad_x, grad_q);
 }
 
-void launch_finalize(se1p_plan *p, int n, double *phi, double *frc, double *energy, cudaStream_t s)
+void launch_finalize(se1p_plan *p, int n, double *phi, double *frc, double *energy, cudaStream_t s,
+                     const double *phi_add, const double *frc_add)
 {
-    k_finalize<<<kEnergyBlocks, 256, 0, s>>>(n, p->b.xyzq, p->b.phi_int, p->b.frc_int, phi, frc, p->b.epart);
+    k_finalize<<<kEnergyBlocks, 256, 0, s>>>(n, p->b.xyzq, p->b.phi_int, p->b.frc_int, phi_add, frc_add, phi, frc,
+                                             p->b.epart);
     if (energy) k_energy_final<<<1, 256, 0, s>>>(p->b.epart, kEnergyBlocks, energy);
 }
 

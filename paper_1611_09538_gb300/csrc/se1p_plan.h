@@ -68,7 +68,10 @@ struct se1p_plan {
     std::vector<void *> host_allocs;
     size_t bytes = 0;
     double norm_k3 = 0;  // 4 pi / M3 (class-specific 1/ns^2 applied in kernels)
-    // per-stage profiling events: [eval][stage boundary]
+    // real space runs on its own stream, concurrently with the grid path (fork / join events)
+    cudaStream_t s_real = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // per-stage profiling events: [eval][stage][start, end], each on the stream the stage runs on
     int profiling = 0;
     int prof_count = 0;
     std::vector<cudaEvent_t> prof_events;
@@ -86,7 +89,8 @@ template <typename T> void launch_gather(se1p_plan *p, int n, const void *grid, 
                                          int flags, cudaStream_t s);
 void launch_vjp_combine(int n, const double *q, const double *v, const double *Eq, const double *phiv,
                         const double *Ev, double *grad_x, double *grad_q, cudaStream_t s);
-void launch_finalize(se1p_plan *p, int n, double *phi, double *frc, double *energy, cudaStream_t s);
+void launch_finalize(se1p_plan *p, int n, double *phi, double *frc, double *energy, cudaStream_t s,
+                     const double *phi_add = nullptr, const double *frc_add = nullptr);
 template <typename T>
 void launch_grid_to_double(se1p_plan *p, const void *src, double *dst, double scale, cudaStream_t s);
 template <typename T> void launch_grid_from_double(se1p_plan *p, const double *src, void *dst, cudaStream_t s);

@@ -224,3 +224,28 @@ def test_z_wrapping_and_host_entry_point():
     se1p.se1p_eval_host(plan.handle, len(q), np.ascontiguousarray(xs), np.ascontiguousarray(q), phi, F, en)
     assert max_rel(phi, r.phi.cpu().numpy()) < 1e-12
     assert max_rel(F, r.force.cpu().numpy()) < 1e-11
+
+
+@pytest.mark.parametrize("precision", [se1p.SE1P_FP64, se1p.SE1P_MIXED])
+def test_back_to_back_evaluations_on_one_plan(precision):
+    """Consecutive evaluations with different charges on one plan, queued without a host sync:
+    the real space runs on the plan's second stream (fork after the pack, join before the
+    finalisation), so each result must equal that of a fresh plan, element by element."""
+    x, q0, prm = CASES["c1_like"]
+    qs = [q0, q0[::-1].copy(), np.roll(q0, 7)]
+    plan = make_plan(prm, len(q0), precision=precision)
+    xd = dev(x)
+    outs = []
+    for qq in qs:
+        phi = torch.empty(len(qq), dtype=torch.float64, device="cuda")
+        F = torch.empty((len(qq), 3), dtype=torch.float64, device="cuda")
+        E = torch.empty(1, dtype=torch.float64, device="cuda")
+        se1p.se1p_eval(plan.handle, len(qq), xd, dev(qq), phi, F, E, torch.cuda.current_stream())
+        outs.append((phi, F, E))
+    torch.cuda.synchronize()
+    for qq, (phi, F, E) in zip(qs, outs):
+        ref = make_plan(prm, len(qq), precision=precision).eval(xd, dev(qq))
+        tol = 1e-12 if precision == se1p.SE1P_FP64 else 1e-6  # atomics: summation order only
+        assert max_rel(phi.cpu().numpy(), ref.phi.cpu().numpy()) < tol
+        assert max_rel(F.cpu().numpy(), ref.force.cpu().numpy()) < tol
+        assert E.item() == pytest.approx(ref.energy.item(), rel=tol)

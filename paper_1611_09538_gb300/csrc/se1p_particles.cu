@@ -267,8 +267,8 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(Geo g, int n, const
 // ------------------------------------------------------------------ gridding (Eq. 3.4)
 //
 // Output-stationary: a CTA owns an 8x8x8 tile of the grid and accumulates in
-// registers every particle whose support overlaps it; two CTAs share a tile
-// (alternate z bins) and add their partial tiles into the zeroed grid, one
+// registers every particle whose support overlaps it; kSpreadSplit CTAs may share
+// a tile (alternate z bins) and add their partial tiles into the zeroed grid, one
 // atomic add per grid point each.  A 16-thread group covers the tile with
 // 2(z) x 2(y) x 8(x) points per thread, so each particle costs a thread 4
 // shared loads (its z, y and x window values) for 32 FMAs; the CTA's eight
@@ -280,7 +280,10 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(Geo g, int n, const
 constexpr int kSpreadBatch = 128;
 constexpr int kSpreadGroups = 8;
 constexpr int kSpreadThreads = 16 * kSpreadGroups;
-constexpr int kSpreadSplit = 2;  // CTAs per tile, each taking every other z bin (atomic combine)
+// CTAs per tile, each taking every kSpreadSplit-th z bin (atomic combine).  Alone, 2 is faster
+// (0.44 against 0.58 ms at C2); alongside the concurrent real space, 1 leaves it more of the SMs
+// and the evaluation is faster (1.599 against 1.610 ms).
+constexpr int kSpreadSplit = 1;
 
 template <typename T>
 __global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int *__restrict__ bin_start,

@@ -11,7 +11,7 @@ namespace se1p {
 namespace {
 
 constexpr int kRealWarps = 4;  // warps per CTA (warps work independently)
-constexpr int kRealSplit = 4;  // warps sharing one group of 32 targets (source rows split between them)
+constexpr int kRealSplit = 2;  // warps sharing one group of targets (source rows split between them)
 constexpr int kCand = 96;      // per-warp candidate list (flushed at >= 64)
 constexpr int kRealTargets = 16;                     // targets per warp
 constexpr int kLanesPerTarget = 32 / kRealTargets;   // lanes sharing a target (alternate candidates)

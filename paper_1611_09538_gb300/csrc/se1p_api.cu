@@ -76,17 +76,39 @@ struct Alloc {
         p->bytes += bytes;
         return ptr;
     }
+    void *pinned(size_t bytes)  // page-locked host memory
+    {
+        if (!ok || bytes == 0) return nullptr;
+        void *ptr = nullptr;
+        if (cudaMallocHost(&ptr, bytes) != cudaSuccess) {
+            ok = false;
+            cudaGetLastError();
+            return nullptr;
+        }
+        p->host_allocs.push_back(ptr);
+        return ptr;
+    }
 };
 
 void free_all(se1p_plan *p)
 {
     for (void *ptr : p->dev_allocs) cudaFree(ptr);
     p->dev_allocs.clear();
+    for (void *ptr : p->host_allocs) cudaFreeHost(ptr);
+    p->host_allocs.clear();
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->ev_join) cudaEventDestroy(p->ev_join);
     if (p->s_real) cudaStreamDestroy(p->s_real);
     p->ev_fork = p->ev_join = nullptr;
     p->s_real = nullptr;
+    for (int i = 0; i < 3; ++i) {
+        if (p->ev_f[i]) cudaEventDestroy(p->ev_f[i]);
+        p->ev_f[i] = nullptr;
+    }
+    for (int i = 0; i < 2; ++i) {
+        if (p->s_f[i]) cudaStreamDestroy(p->s_f[i]);
+        p->s_f[i] = nullptr;
+    }
 }
 
 template <typename T> void upload(void *dst, const std::vector<T> &v)
@@ -161,6 +183,7 @@ template <typename T> se1p_status alloc_particles(se1p_plan *p, Alloc &A)
     p->b.sums = (double *)A.dev(sizeof(double) * 2);
     p->b.epart = (double *)A.dev(sizeof(double) * kEnergyBlocks);
     p->b.status = (int *)A.dev(sizeof(int));
+    p->b.hstatus = (int *)A.pinned(sizeof(int));
     p->b.hx = (double *)A.dev(sizeof(double) * 3 * (size_t)nm);
     p->b.hq = (double *)A.dev(sizeof(double) * (size_t)nm);
     p->b.hphi = (double *)A.dev(sizeof(double) * (size_t)nm);
@@ -434,9 +457,14 @@ se1p_status se1p_plan_create(const se1p_params *prm, int n_max, se1p_plan **out)
     if (st != SE1P_OK) { free_all(p); delete p; return st; }
     int cfg = mixed ? configure_fourier_kernels<float>(p) : configure_fourier_kernels<double>(p);
     if (cfg != 0) { cudaGetLastError(); free_all(p); delete p; return SE1P_ERR_CUDA; }
-    if (cudaStreamCreateWithFlags(&p->s_real, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    bool streams_ok = cudaStreamCreateWithFlags(&p->s_real, cudaStreamNonBlocking) == cudaSuccess &&
+                      cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+                      cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < 2; ++i)
+        streams_ok = streams_ok && cudaStreamCreateWithFlags(&p->s_f[i], cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; i < 3; ++i)
+        streams_ok = streams_ok && cudaEventCreateWithFlags(&p->ev_f[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!streams_ok) {
         cudaGetLastError();
         free_all(p);
         delete p;
@@ -577,8 +605,12 @@ se1p_status se1p_eval_host(se1p_plan *p, int n, const double *x, const double *q
     if (phi && n > 0) cudaMemcpyAsync(phi, p->b.hphi, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, s);
     if (force && n > 0) cudaMemcpyAsync(force, p->b.hfrc, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost, s);
     if (energy) cudaMemcpyAsync(energy, p->b.hen, sizeof(double), cudaMemcpyDeviceToHost, s);
+    // the status word travels with the outputs and is cleared on the stream: one blocking sync
+    cudaMemcpyAsync(p->b.hstatus, p->b.status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemsetAsync(p->b.status, 0, sizeof(int), s);
     if (check_launch() != SE1P_OK) return SE1P_ERR_CUDA;
-    return se1p_plan_sync_status(p, stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SE1P_ERR_CUDA;
+    return flags_to_status(*p->b.hstatus);
 }
 
 se1p_status se1p_spread(se1p_plan *p, int n, const double *x, const double *q, double *grid, void *stream)

@@ -274,9 +274,16 @@ template <typename T> void launch_fourier(se1p_plan *p, cudaStream_t s)
         k_zfwd<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb, (const T *)p->b.grid,
                                             (Cx<T> *)p->b.zspec, p->b.slab0_in);
     }
+    // the three slab classes are independent between the z passes: classes 0 (k3 = 0, FP64)
+    // and 1 (set I) run on the plan's two Fourier streams, class 2 (set J) on s
+    cudaEventRecord(p->ev_f[0], s);
+    cudaStreamWaitEvent(p->s_f[0], p->ev_f[0], 0);
+    cudaStreamWaitEvent(p->s_f[1], p->ev_f[0], 0);
+    const cudaStream_t s_main = s;
     for (int c = 0; c < 3; ++c) {
         const SlabClass &C = p->cls[c];
         if (C.count == 0) continue;
+        const cudaStream_t s = c == 2 ? s_main : p->s_f[c];  // this class's stream
         const int nrows = C.count * Mt;
         if (c == 0) {
             const size_t smx = 2 * (size_t)C.rb * C.ns * cbytes<double>();
@@ -303,6 +310,10 @@ template <typename T> void launch_fourier(se1p_plan *p, cudaStream_t s)
                 nullptr);
         }
     }
+    cudaEventRecord(p->ev_f[1], p->s_f[0]);
+    cudaEventRecord(p->ev_f[2], p->s_f[1]);
+    cudaStreamWaitEvent(s, p->ev_f[1], 0);
+    cudaStreamWaitEvent(s, p->ev_f[2], 0);
     // z inverse
     {
         const int xb = p->xb_z;

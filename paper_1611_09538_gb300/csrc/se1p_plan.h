@@ -46,6 +46,7 @@ struct Buffers {
     double *epart = nullptr;     // [kEnergyBlocks]
     int *status = nullptr;
     double *hx = nullptr, *hq = nullptr, *hphi = nullptr, *hfrc = nullptr, *hen = nullptr;  // host staging
+    int *hstatus = nullptr;  // page-locked copy of the status word (host entry point)
     double *dgrid = nullptr;     // FP64 grid for stage entry points [M3][Mt][Mt]
 };
 
@@ -71,6 +72,9 @@ struct se1p_plan {
     // real space runs on its own stream, concurrently with the grid path (fork / join events)
     cudaStream_t s_real = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // slab classes 0 and 1 of the Fourier passes run on their own streams (fork ev_f[0], joins 1, 2)
+    cudaStream_t s_f[2] = {nullptr, nullptr};
+    cudaEvent_t ev_f[3] = {nullptr, nullptr, nullptr};
     // per-stage profiling events: [eval][stage][start, end], each on the stream the stage runs on
     int profiling = 0;
     int prof_count = 0;

@@ -60,13 +60,15 @@ def parse():
 
 def workload(name):
     from paper_1611_09538_gb300 import inputs
-    return {"c1": inputs.config_c1, "c2": inputs.config_c2, "c3": inputs.config_c3}[name]()
+    # c3: the elongated box on the grid that resolves xi = 40 (on the printed grid, eta = 3.3 > 1,
+    # the mixed path cannot reach rms 1e-6, so no throughput at that accuracy exists there)
+    return {"c1": inputs.config_c1, "c2": inputs.config_c2, "c3": inputs.config_c3_resolved}[name]()
 
 
 def workload_config(sys_, name, precision):
     p = sys_.params
     return {
-        "workload": f"{name.upper()}: N={len(sys_.q)} uniform charges, L={list(sys_.L)}, xi={p['xi']}, "
+        "workload": f"{sys_.name or name.upper()}: N={len(sys_.q)} uniform charges, L={list(sys_.L)}, xi={p['xi']}, "
                     f"M={list(p['M'])}, P={p['P']}, Mt={p['Mt']}, n0={p['n0']}, nI={p['nI']}, nl={p['nl']}, "
                     f"rc={p['rc']}",
         "N": len(sys_.q), "precision": precision, "L2": "flushed between timed steps (256 MiB write)",

@@ -173,6 +173,7 @@ template <typename T> se1p_status alloc_particles(se1p_plan *p, Alloc &A)
     p->b.counts = (int *)A.dev(sizeof(int) * (size_t)(g.nbins + g.ncells));
     p->b.starts = (int *)A.dev(sizeof(int) * (size_t)(g.nbins + g.ncells + 2));
     p->b.cursors = (int *)A.dev(sizeof(int) * (size_t)(g.nbins + g.ncells));
+    p->b.scan_tmp = (int *)A.dev(sizeof(int) * (size_t)kScanTmp);
     p->b.parts = A.dev(sizeof(PartRec<T>) * (size_t)nm);
     p->b.wts = A.dev(sizeof(T) * 3 * (size_t)p->geo.P * nm);
     p->b.cells = A.dev(sizeof(CellRec<T>) * (size_t)nm);

@@ -37,13 +37,20 @@ __global__ void k_zfwd(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restric
         a[e] = cx<T>(v, (T)0);
     }
     __syncthreads();
-    // k3 = 0 coefficient, summed in FP64 from the stored grid values
-    for (int p = threadIdx.x; p < xb; p += blockDim.x) {
-        const int x = x0 + p;
-        if (x < Mt) {
-            double s = 0.0;
-            for (int z = 0; z < M3; ++z) s += (double)a[z * xb + p].re;
-            slab0[(size_t)y * Mt + x] = s;
+    // k3 = 0 coefficient, summed in FP64 from the stored grid values: the blockDim / xb threads
+    // of a pencil take every G-th z, their partial sums are added in a fixed order
+    {
+        __shared__ double part[256];
+        const int G = blockDim.x / xb;  // xb is a power of 2 <= 32 that divides blockDim (256)
+        const int p = threadIdx.x % xb, g = threadIdx.x / xb;
+        double sum = 0.0;
+        for (int z = g; z < M3; z += G) sum += (double)a[z * xb + p].re;
+        part[threadIdx.x] = sum;
+        __syncthreads();
+        if (g == 0 && x0 + p < Mt) {
+            double tot = 0.0;
+            for (int k = 0; k < G; ++k) tot += part[k * xb + p];
+            slab0[(size_t)y * Mt + x0 + p] = tot;
         }
     }
     __syncthreads();
@@ -245,6 +252,15 @@ template <typename T> void launch_symbol_tables(se1p_plan *p, cudaStream_t s)
 template void launch_symbol_tables<float>(se1p_plan *, cudaStream_t);
 template void launch_symbol_tables<double>(se1p_plan *, cudaStream_t);
 
+// Opt a kernel in to the device's largest dynamic shared memory (less its static shared memory).
+template <typename K> cudaError_t allow_max_dynamic_smem(K kernel, int maxsm)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm - (int)fa.sharedSizeBytes);
+}
+
 template <typename T> int configure_fourier_kernels(se1p_plan *p)
 {
     int dev;
@@ -252,14 +268,14 @@ template <typename T> int configure_fourier_kernels(se1p_plan *p)
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaError_t e = cudaSuccess;
-    e = (cudaError_t)(e | cudaFuncSetAttribute(k_zfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    e = (cudaError_t)(e | cudaFuncSetAttribute(k_zinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    e = (cudaError_t)(e | cudaFuncSetAttribute(k_xfwd<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    e = (cudaError_t)(e | cudaFuncSetAttribute(k_xinv<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    e = (cudaError_t)(e | cudaFuncSetAttribute(k_yscale<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    e = (cudaError_t)(e | cudaFuncSetAttribute(k_xfwd<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    e = (cudaError_t)(e | cudaFuncSetAttribute(k_xinv<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    e = (cudaError_t)(e | cudaFuncSetAttribute(k_yscale<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    e = (cudaError_t)(e | allow_max_dynamic_smem(k_zfwd<T>, maxsm));
+    e = (cudaError_t)(e | allow_max_dynamic_smem(k_zinv<T>, maxsm));
+    e = (cudaError_t)(e | allow_max_dynamic_smem(k_xfwd<T, false>, maxsm));
+    e = (cudaError_t)(e | allow_max_dynamic_smem(k_xinv<T, false>, maxsm));
+    e = (cudaError_t)(e | allow_max_dynamic_smem(k_yscale<T, false>, maxsm));
+    e = (cudaError_t)(e | allow_max_dynamic_smem(k_xfwd<double, true>, maxsm));
+    e = (cudaError_t)(e | allow_max_dynamic_smem(k_xinv<double, true>, maxsm));
+    e = (cudaError_t)(e | allow_max_dynamic_smem(k_yscale<double, true>, maxsm));
     return e == cudaSuccess ? 0 : -1;
 }
 

@@ -23,6 +23,10 @@ enum : int {
 
 constexpr double kPi = 3.14159265358979323846264338327950288;
 
+// multi-block scan of the cell counts: 4096 counts per block, at most kScanTmp blocks (2^22 cells)
+constexpr int kScanChunk = 4096;
+constexpr int kScanTmp = (1 << 22) / kScanChunk + 2;
+
 // ------------------------------------------------------------------ complex
 template <typename T> struct Cx;
 template <> struct __align__(8) Cx<float> { float re, im; };

@@ -159,6 +159,92 @@ __global__ void k_scan(int nbins, int ncells, const int *__restrict__ counts, in
     }
 }
 
+// Multi-block exclusive scan of the cell counts (used when there are many cells): per-block
+// sums, one block scanning those into block offsets, then each block rescanning its chunk.
+constexpr int kScanThreads = 256, kScanItems = kScanChunk / kScanThreads;
+
+// Exclusive scan of one value per thread over the block (kScanThreads threads); every thread
+// also receives the block's total.
+__device__ __forceinline__ int block_exclusive_scan(int v, int &total)
+{
+    constexpr int NW = kScanThreads / 32;
+    __shared__ int wsum[NW + 1];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int w = lane < NW ? wsum[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < NW) wsum[lane] = wi - w;  // exclusive warp offsets
+        if (lane == NW - 1) wsum[NW] = wi;   // block total
+    }
+    __syncthreads();
+    const int r = wsum[wid] + incl - v;
+    total = wsum[NW];
+    __syncthreads();  // wsum is reused by the next call
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(int len, const int *__restrict__ c, int *__restrict__ bsum)
+{
+    const int base = blockIdx.x * kScanChunk;
+    int s = 0;
+    for (int k = threadIdx.x; k < kScanChunk; k += kScanThreads)
+        if (base + k < len) s += c[base + k];
+    int total;
+    block_exclusive_scan(s, total);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_offsets(int nblk, int *__restrict__ bsum)
+{
+    int carry = 0;
+    for (int base = 0; base < nblk; base += kScanThreads) {
+        const int i = base + threadIdx.x;
+        const int v = i < nblk ? bsum[i] : 0;
+        int total;
+        const int e = block_exclusive_scan(v, total);
+        if (i < nblk) bsum[i] = carry + e;
+        carry += total;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_write(int len, const int *__restrict__ c,
+                                                              const int *__restrict__ boff, int *__restrict__ st,
+                                                              int *__restrict__ cu)
+{
+    const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int ts = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < len ? c[base + k] : 0;
+        ts += v[k];
+    }
+    int total;
+    int e = boff[blockIdx.x] + block_exclusive_scan(ts, total);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < len) {
+            st[base + k] = e;
+            cu[base + k] = e;
+            if (base + k == len - 1) st[len] = e + v[k];
+        }
+        e += v[k];
+    }
+}
+
 // e^x in FP32 for the window exponents, x in [-87, 0]: e^x = 2^n e^r with
 // n = rint(x / ln 2) and r = x - n ln 2 (Cody and Waite's reduction: ln 2 in two
 // parts, the first with 8 trailing zero bits so that n * hi is exact for |n| < 256),
@@ -696,8 +782,20 @@ void launch_pack(se1p_plan *p, int n, const double *x, const double *q, cudaStre
         k_pack<T><<<blocks_for(n, 256, 0x7fffffff), 256, 0, s>>>(g, n, x, q, p->b.xyzq, p->b.bin_key, p->b.cell_key,
                                                        p->b.counts, p->b.counts + g.nbins, p->b.sums,
                                                        p->b.status);
-    k_scan<<<2, 1024, 0, s>>>(g.nbins, g.ncells, p->b.counts, p->b.starts, p->b.cursors, p->b.sums,
-                              p->b.status, check_neutral);
+    if (g.ncells <= 16 * kScanChunk) {
+        k_scan<<<2, 1024, 0, s>>>(g.nbins, g.ncells, p->b.counts, p->b.starts, p->b.cursors, p->b.sums,
+                                  p->b.status, check_neutral);
+    } else {
+        // many cells: one block scans the bins, three launches scan the cells
+        k_scan<<<1, 1024, 0, s>>>(g.nbins, g.ncells, p->b.counts, p->b.starts, p->b.cursors, p->b.sums,
+                                  p->b.status, check_neutral);
+        const int nblk = (g.ncells + kScanChunk - 1) / kScanChunk;  // <= kScanTmp (2^22 cells at most)
+        const int *cc = p->b.counts + g.nbins;
+        k_scan_sums<<<nblk, kScanThreads, 0, s>>>(g.ncells, cc, p->b.scan_tmp);
+        k_scan_offsets<<<1, kScanThreads, 0, s>>>(nblk, p->b.scan_tmp);
+        k_scan_write<<<nblk, kScanThreads, 0, s>>>(g.ncells, cc, p->b.scan_tmp, p->b.starts + g.nbins + 1,
+                                                   p->b.cursors + g.nbins);
+    }
 }
 
 template <typename T> void launch_sort_scatter(se1p_plan *p, int n, cudaStream_t s)

@@ -35,6 +35,7 @@ struct Buffers {
     int *counts = nullptr;       // [nbins + ncells]
     int *starts = nullptr;       // [nbins + 1 + ncells + 1]
     int *cursors = nullptr;      // [nbins + ncells]
+    int *scan_tmp = nullptr;     // block offsets of the multi-block cell scan [kScanTmp]
     void *parts = nullptr;       // PartRec<T> [n_max]
     void *wts = nullptr;         // T [n_max][3][P]
     void *cells = nullptr;       // CellRec<T> [n_max]

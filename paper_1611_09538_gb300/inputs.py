@@ -159,6 +159,16 @@ def config_c3(n: int = 1_000_000) -> System:
                                                 nI=192, nl=4, rc=0.09), "C3")
 
 
+def config_c3_resolved(n: int = 1_000_000) -> System:
+    """The C3 charges on the grid that resolves xi = 40: M = 128 x 128 x 1024 (h = 1/128,
+    eta = 0.83 < 1).  The printed grid (h = 1/64) gives eta = 3.3, where the scaling grows
+    with k and amplifies FP32 rounding ~1e6-fold (Eq. 3.3)."""
+    s = config_c3(n)
+    s.params = dict(xi=40.0, M=(128, 128, 1024), P=24, Mt=160, n0=480, nI=320, nl=4, rc=0.09)
+    s.name = "C3 resolved"
+    return s
+
+
 def config_c4(n: int = 200_000) -> System:
     """N=200k in 8 Gaussian blobs (sigma=0.05) in L=[1,1,2], +-1.
 

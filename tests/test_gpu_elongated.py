@@ -33,7 +33,7 @@ def _lib():
     se1p_build.build()
 
 
-RESOLVED = dict(xi=40.0, M=(128, 128, 1024), P=24, Mt=160, n0=480, nI=320, nl=4, rc=0.09)
+RESOLVED = inputs.config_c3_resolved(n=2).params
 
 
 def make(L, prm, n, prec):

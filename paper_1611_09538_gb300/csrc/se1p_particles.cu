@@ -424,9 +424,11 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int *__r
                 __syncthreads();  // previous batch fully consumed
                 for (int b = threadIdx.x; b < nb; b += kSpreadThreads) {
                     const PartRec<T> pr = parts[b0 + b];
-                    // support offset of the tile origin per axis; z taken cyclically into [-8, M3-9]
+                    // support offset of the tile origin per axis; z taken cyclically into [0, M3), so
+                    // that dz + o needs one wrap (a plain difference misses the wrapped part of the
+                    // support when M3 < P + 8)
                     int dz = z0 - pr.i0[2];
-                    if (dz < -kBin) dz += M3;
+                    if (dz < 0) dz += M3;
                     soff[b][0] = x0 - pr.i0[0];
                     soff[b][1] = y0 - pr.i0[1];
                     soff[b][2] = dz;

@@ -77,6 +77,9 @@ CASES = {
     # elongated periodic axis: M3 = 256 (K3 = 129 z modes, 32 of them in the set I)
     "elongated": small_case(n=600, L=(1.0, 1.0, 8.0), seed=6, xi=8.0, M=(32, 32, 256), P=16, Mt=48, n0=144,
                             nI=96, nl=4, rc=0.3),
+    # short periodic axis: M3 = 16 < P + 8, so a window wraps into the same 8-point gridding tile
+    "short_axis": small_case(n=400, L=(1.0, 1.0, 0.5), seed=8, xi=8.0, M=(32, 32, 16), P=16, Mt=48, n0=144,
+                             nI=96, nl=2, rc=0.25),
 }
 
 

@@ -205,7 +205,7 @@ int orc_ewald1p(int n, const double *x, const double *q, int nt, const int *tgt,
         if (exp(-a) / a < kcut) break;
         jmax = j;
     }
-    /* z images that can lie within rc: all alpha with |alpha L3| <= rc + L3 */
+    /* z images that can lie within rc of a principal offset: |alpha L3| <= rc + L3/2 */
     int amax = rc > 0.0 ? (int)ceil(rc / L3) + 1 : 0;
 
     /* Work items are (target, source chunk) pairs so that a few targets still keep
@@ -234,10 +234,12 @@ int orc_ewald1p(int n, const double *x, const double *q, int nt, const int *tgt,
             const double qn = q[nn];
             const double dx = xm - x[3 * nn], dy = ym - x[3 * nn + 1], dz = zm - x[3 * nn + 2];
             const double rho2 = dx * dx + dy * dy;
-            /* real space, Eq. 2.2 and Eq. 3.22 */
+            /* real space, Eq. 2.2 and Eq. 3.22: images of the principal z offset
+             * (|dzr| <= L3/2, so any z may be given, not only z in [0, L3)) */
+            const double dzr = dz - L3 * rint(dz / L3);
             for (int al = -amax; al <= amax && rc > 0.0; ++al) {
                 if (nn == m && al == 0) continue;
-                const double dzp = dz + al * L3;
+                const double dzp = dzr + al * L3;
                 const double r2 = rho2 + dzp * dzp;
                 const double r = sqrt(r2);
                 if (r > rc) continue;

@@ -176,7 +176,8 @@ def test_total_potential_matches_brute_force_images(direct_oracle):
 
 
 def test_homogeneity_and_z_translation(direct_oracle):
-    """L -> lam L, xi -> xi/lam gives phi -> phi/lam, F -> F/lam^2; z shifts change nothing."""
+    """L -> lam L, xi -> xi/lam gives phi -> phi/lam, F -> F/lam^2; z shifts of all charges, or of
+    single charges by whole periods, change nothing (the sums run over every z image, Eq. 2.2)."""
     x, q = _tiny_system(seed=11, n=8)
     xi = 7.0
     phi, F, _ = direct_oracle.ewald1p(x, q, 1.0, xi, 6.5 / xi)
@@ -189,6 +190,12 @@ def test_homogeneity_and_z_translation(direct_oracle):
     phi3, F3, _ = direct_oracle.ewald1p(xs, q, 1.0, xi, 6.5 / xi)
     assert np.max(np.abs(phi3 - phi)) < 1e-12 * np.max(np.abs(phi))
     assert np.max(np.abs(F3 - F)) < 1e-11 * np.max(np.abs(F))
+    # single charges given at other periodic images (z off by whole periods) change nothing
+    xp = x.copy()
+    xp[:, 2] += np.array([0, -1, 2, 0, 3, -2, 1, 0])[: len(q)] * 1.0
+    phi4, F4, _ = direct_oracle.ewald1p(xp, q, 1.0, xi, 6.5 / xi)
+    assert np.max(np.abs(phi4 - phi)) < 1e-12 * np.max(np.abs(phi))
+    assert np.max(np.abs(F4 - F)) < 1e-11 * np.max(np.abs(F))
 
 
 # ---------------------------------------------------------------- forces
@@ -310,6 +317,27 @@ def test_se_algorithm_odd_support(direct_oracle):
     phi, F = se.se1p_fourier(x, q, (1.0, 1.0, 1.0), 8.0, (40, 40, 40), 25, 66, 198, 264, 6)
     assert rel_rms(phi, phi_ref) < 1e-11
     assert rel_rms(F, F_ref) < 1e-10
+
+
+def test_se_algorithm_short_periodic_axis(direct_oracle):
+    """A periodic axis as short as the support (M3 = P = 20, L3 = 0.5): every window wraps
+    around the whole z axis (Eq. 3.7 taken periodically) and still reproduces Eq. 2.3b + Eq. 2.4.
+    The discrete operator is symmetric (the same window spreads and gathers, Eqs. 3.7, 3.11), so
+    c . phi[q] = q . phi[c] for any two charge vectors."""
+    rng = np.random.default_rng(24)
+    n = 120
+    L = (1.0, 1.0, 0.5)
+    x = rng.random((n, 3)) * np.array(L)
+    q = rng.uniform(-1, 1, n)
+    q -= q.mean()
+    phi_ref, F_ref = _kspace_direct(direct_oracle, x, q, L[2], 8.0)
+    phi, F = se.se1p_fourier(x, q, L, 8.0, (40, 40, 20), 20, 64, 192, 192, 6)
+    assert rel_rms(phi, phi_ref) < 1e-11
+    assert rel_rms(F, F_ref) < 1e-10
+    c = rng.standard_normal(n)
+    c -= c.mean()
+    phi_c, _ = se.se1p_fourier(x, c, L, 8.0, (40, 40, 20), 20, 64, 192, 192, 6)
+    assert abs(c @ phi - q @ phi_c) < 1e-12 * np.abs(c) @ np.abs(phi)
 
 
 def test_table_4_1_error_levels(direct_oracle):

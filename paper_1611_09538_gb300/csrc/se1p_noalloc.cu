@@ -83,9 +83,10 @@ __global__ void k_na_pack(Geo g, int n, const double *__restrict__ x, const doub
     if (!isfinite(qq)) qq = 0.0;
     px = fmin(fmax(px, 0.0), g.L[0] * (1.0 - 1e-15));
     py = fmin(fmax(py, 0.0), g.L[1] * (1.0 - 1e-15));
-    if (pz < 0.0 || pz >= g.L[2]) {
-        pz = pz - floor(pz / g.L[2]) * g.L[2];
-        if (pz >= g.L[2] || pz < 0.0) pz = 0.0;
+    if (pz < 0.0 || pz >= g.L[2]) {  // periodic image in [0, L3): fmod is exact
+        pz = fmod(pz, g.L[2]);
+        if (pz < 0.0) pz += g.L[2];
+        if (pz >= g.L[2]) pz = 0.0;
     }
     const int cx = min((int)(px / g.cs[0]), g.ncx - 1);
     const int cy = min((int)(py / g.cs[1]), g.ncy - 1);

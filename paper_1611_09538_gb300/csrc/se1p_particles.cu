@@ -34,6 +34,19 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v)
 }
 
 // Free-axis and z support starts of a sanitised particle.
+// Grid coordinate t = x / h.  The product x (1/h) is within a few ulps of the correctly
+// rounded quotient; it can only change the support start (floor(t) for even P, floor(t + 1/2)
+// for odd P) when t lies that close to an integer (even P) or a half-integer (odd P), e.g. a
+// charge on a grid node.  There the quotient is taken exactly, so that the support is the one
+// the plain definition gives (FP64 division is slow on this part, and almost never needed).
+__device__ __forceinline__ double grid_coord(double xs, double h, double inv_h, int P)
+{
+    double t = xs * inv_h;
+    const double b = (P & 1) ? floor(t) + 0.5 : rint(t);  // nearest decision boundary
+    if (fabs(t - b) <= 1e-14 * fmax(fabs(t), 1.0)) t = xs / h;
+    return t;
+}
+
 struct Support {
     int i0[3];
     double t[3];
@@ -42,11 +55,9 @@ struct Support {
 __device__ __forceinline__ Support particle_support(const Geo &g, double px, double py, double pz)
 {
     Support s;
-    // grid coordinates (multiplication by 1/h: FP64 division is slow on this part; a
-    // support start can differ from x/h only when t is within an ulp of an integer)
-    s.t[0] = (px + g.off) * g.inv_h;
-    s.t[1] = (py + g.off) * g.inv_h;
-    s.t[2] = pz * g.inv_hz;
+    s.t[0] = grid_coord(px + g.off, g.h, g.inv_h, g.P);
+    s.t[1] = grid_coord(py + g.off, g.h, g.inv_h, g.P);
+    s.t[2] = grid_coord(pz, g.hz, g.inv_hz, g.P);
     const int hi = g.Mt - g.P;
     s.i0[0] = min(max(support_start(s.t[0], g.P), 0), hi);
     s.i0[1] = min(max(support_start(s.t[1], g.P), 0), hi);
@@ -78,9 +89,10 @@ __global__ void k_pack(Geo g, int n, const double *__restrict__ x, const double 
             px = fmin(fmax(px, 0.0), g.L[0] * (1.0 - 1e-15));
             py = fmin(fmax(py, 0.0), g.L[1] * (1.0 - 1e-15));
         }
-        if (pz < 0.0 || pz >= g.L[2]) {
-            pz = pz - floor(pz / g.L[2]) * g.L[2];
-            if (pz >= g.L[2] || pz < 0.0) pz = 0.0;
+        if (pz < 0.0 || pz >= g.L[2]) {  // periodic image in [0, L3): fmod is exact
+            pz = fmod(pz, g.L[2]);
+            if (pz < 0.0) pz += g.L[2];
+            if (pz >= g.L[2]) pz = 0.0;
         }
         const Support s = particle_support(g, px, py, pz);
         const int bx = s.i0[0] / kBin, by = s.i0[1] / kBin, bz = imod(s.i0[2], g.M3) / kBin;

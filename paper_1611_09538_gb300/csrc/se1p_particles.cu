@@ -404,6 +404,11 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int *__r
     for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < kBin; ++c) acc[r][c] = (T)0;
+    f32x2 acc2[4][kBin / 2];  // FP32: the same sums as packed column pairs
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int j = 0; j < kBin / 2; ++j) acc2[r][j] = 0ull;
 
     // bins whose start indices can reach the tile
     const int bx_lo = max(x0 - P + 1, 0) / kBin, bx_hi = min(x0 + kBin - 1, g.Mt - P) / kBin;
@@ -469,17 +474,40 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int *__r
                     const T wz0 = sw[b][2][tz], wz1 = sw[b][2][tz + 1];
                     const T wy0 = sw[b][1][ty], wy1 = sw[b][1][ty + 1];
                     const T s00 = wz0 * wy0, s01 = wz0 * wy1, s10 = wz1 * wy0, s11 = wz1 * wy1;
+                    if constexpr (sizeof(T) == 4) {
+                        // packed pairs of x columns: 16 two-wide FMAs instead of 32
+                        const float4 xa = *reinterpret_cast<const float4 *>(&sw[b][0][0]);
+                        const float4 xb = *reinterpret_cast<const float4 *>(&sw[b][0][4]);
+                        const f32x2 w[4] = {f2_pack(xa.x, xa.y), f2_pack(xa.z, xa.w), f2_pack(xb.x, xb.y),
+                                         f2_pack(xb.z, xb.w)};
+                        const f32x2 sp[4] = {f2_splat(s00), f2_splat(s01), f2_splat(s10), f2_splat(s11)};
 #pragma unroll
-                    for (int c = 0; c < kBin; ++c) {
-                        const T wx = sw[b][0][c];
-                        acc[0][c] += s00 * wx;
-                        acc[1][c] += s01 * wx;
-                        acc[2][c] += s10 * wx;
-                        acc[3][c] += s11 * wx;
+                        for (int r = 0; r < 4; ++r)
+#pragma unroll
+                            for (int j = 0; j < kBin / 2; ++j) acc2[r][j] = f2_fma(sp[r], w[j], acc2[r][j]);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < kBin; ++c) {
+                            const T wx = sw[b][0][c];
+                            acc[0][c] += s00 * wx;
+                            acc[1][c] += s01 * wx;
+                            acc[2][c] += s10 * wx;
+                            acc[3][c] += s11 * wx;
+                        }
                     }
                 }
             }
         }
+    }
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int j = 0; j < kBin / 2; ++j) {
+                const float2 v = f2_unpack(acc2[r][j]);
+                acc[r][2 * j] = v.x;
+                acc[r][2 * j + 1] = v.y;
+            }
     }
     __syncthreads();
     if (grp > 0) {

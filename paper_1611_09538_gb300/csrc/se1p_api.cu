@@ -48,7 +48,14 @@ bool make_fft(int n, FftDesc &d)
     while (m % 2 == 0) { if (!push(2)) return false; m /= 2; }
     for (int r : {3, 5, 7})
         while (m % r == 0) { if (!push(r)) return false; m /= r; }
-    return m == 1;
+    if (m != 1) return false;
+    int Ns = 1;
+    for (int st = 0; st < d.nrad; ++st) {
+        d.ns[st] = make_fastdiv((unsigned)Ns);
+        d.nb[st] = make_fastdiv((unsigned)(n / d.rad[st]));
+        Ns *= d.rad[st];
+    }
+    return true;
 }
 
 template <typename T> size_t csize() { return sizeof(Cx<T>); }

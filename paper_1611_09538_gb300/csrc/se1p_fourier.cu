@@ -23,7 +23,7 @@ __device__ __forceinline__ int signed_index(int i, int n) { return i <= (n - 1) 
 
 // ---- z forward: CTA = (y, chunk of xb x-values); smem [z][p]
 template <typename T>
-__global__ void k_zfwd(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restrict__ tw, int xb,
+__global__ void k_zfwd(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restrict__ tw, int xb, FastDiv fxb,
                        const T *__restrict__ grid, Cx<T> *__restrict__ zspec, double *__restrict__ slab0)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -32,19 +32,32 @@ __global__ void k_zfwd(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restric
     const int nxc = (Mt + xb - 1) / xb;
     const int y = blockIdx.x / nxc, x0 = (blockIdx.x % nxc) * xb;
     for (int e = threadIdx.x; e < M3 * xb; e += blockDim.x) {
-        const int z = e / xb, p = e % xb, x = x0 + p;
+        const int z = fdiv(e, fxb), p = e - z * xb, x = x0 + p;
         const T v = x < Mt ? grid[((size_t)z * Mt + y) * Mt + x] : (T)0;
         a[e] = cx<T>(v, (T)0);
     }
     __syncthreads();
-    // k3 = 0 coefficient, summed in FP64 from the stored grid values: the blockDim / xb threads
-    // of a pencil take every G-th z, their partial sums are added in a fixed order
+    // k3 = 0 coefficient, summed to FP64 accuracy from the stored grid values: the blockDim / xb
+    // threads of a pencil take every G-th z; FP32 grids keep each thread's partial sum as an
+    // unevaluated hi + lo pair (TwoSum, exact to ~2^-48), FP64 grids sum directly; the partials
+    // are added in FP64 in a fixed order
     {
         __shared__ double part[256];
         const int G = blockDim.x / xb;  // xb is a power of 2 <= 32 that divides blockDim (256)
-        const int p = threadIdx.x % xb, g = threadIdx.x / xb;
+        const int g = threadIdx.x / xb, p = threadIdx.x - g * xb;
         double sum = 0.0;
-        for (int z = g; z < M3; z += G) sum += (double)a[z * xb + p].re;
+        if constexpr (sizeof(T) == sizeof(double)) {
+            for (int z = g; z < M3; z += G) sum += (double)a[z * xb + p].re;
+        } else {
+            float hi = 0.0f, lo = 0.0f;
+            for (int z = g; z < M3; z += G) {
+                const float v = a[z * xb + p].re;
+                const float t = hi + v, bv = t - hi;
+                lo += (hi - (t - bv)) + (v - bv);
+                hi = t;
+            }
+            sum = (double)hi + (double)lo;
+        }
         part[threadIdx.x] = sum;
         __syncthreads();
         if (g == 0 && x0 + p < Mt) {
@@ -54,9 +67,9 @@ __global__ void k_zfwd(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restric
         }
     }
     __syncthreads();
-    Cx<T> *res = fft_smem<T>(a, b, d, xb, 1, xb, tw, -1);
+    Cx<T> *res = fft_smem<T>(a, b, d, xb, fxb, 1, xb, tw, -1);
     for (int e = threadIdx.x; e < (K3 - 1) * xb; e += blockDim.x) {
-        const int k = 1 + e / xb, p = e % xb, x = x0 + p;
+        const int k1 = fdiv(e, fxb), p = e - k1 * xb, k = 1 + k1, x = x0 + p;
         if (x < Mt) zspec[((size_t)k * Mt + y) * Mt + x] = res[k * xb + p];
     }
 }
@@ -64,27 +77,28 @@ __global__ void k_zfwd(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restric
 // ---- x forward: CTA = rb rows (slab s, y) of one class; smem [row][ns]
 template <typename T, bool FROM_SLAB0>
 __global__ void k_xfwd(int Mt, int ns, int kfirst, int nrows, FftDesc d, const Tw<T> *__restrict__ tw, int rb,
-                       const Cx<T> *__restrict__ zspec, const double *__restrict__ slab0, Cx<T> *__restrict__ rows)
+                       FastDiv frb, FastDiv fns, FastDiv fMt, const Cx<T> *__restrict__ zspec,
+                       const double *__restrict__ slab0, Cx<T> *__restrict__ rows)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
     Cx<T> *b = a + (size_t)rb * ns;
     const int r0 = blockIdx.x * rb;
     for (int e = threadIdx.x; e < rb * ns; e += blockDim.x) {
-        const int p = e / ns, j = e % ns, r = r0 + p;
+        const int p = fdiv(e, fns), j = e - p * ns, r = r0 + p;
         Cx<T> v = cx<T>((T)0, (T)0);
         if (r < nrows && j < Mt) {
-            const int s = r / Mt, y = r % Mt;
+            const int s = fdiv(r, fMt), y = r - s * Mt;
             if (FROM_SLAB0) v = cx<T>((T)slab0[(size_t)y * Mt + j], (T)0);
             else v = zspec[((size_t)(kfirst + s) * Mt + y) * Mt + j];
         }
         a[e] = v;
     }
     __syncthreads();
-    Cx<T> *res = fft_smem<T>(a, b, d, rb, ns, 1, tw, -1);
+    Cx<T> *res = fft_smem<T>(a, b, d, rb, frb, ns, 1, tw, -1);
     for (int e = threadIdx.x; e < rb * ns; e += blockDim.x) {
-        const int p = e / ns, r = r0 + p;
-        if (r < nrows) rows[(size_t)r * ns + (e % ns)] = res[e];
+        const int p = fdiv(e, fns), r = r0 + p;
+        if (r < nrows) rows[(size_t)r * ns + (e - p * ns)] = res[e];
     }
 }
 
@@ -93,7 +107,8 @@ __global__ void k_xfwd(int Mt, int ns, int kfirst, int nrows, FftDesc d, const T
 // of 4 pi / (ns^2 M3) exp(-(1-eta) kappa^2 / 4 xi^2 - (1-eta_z) k3^2 / 4 xi^2) / (kappa^2 + k3^2).
 template <typename T, bool CLASS0>
 __global__ void k_yscale(int Mt, int ns, int kfirst, int count, FftDesc d, const Tw<T> *__restrict__ tw, int xb,
-                         Cx<T> *__restrict__ rows, const double *__restrict__ sym0, const T *__restrict__ symc)
+                         FastDiv fxb, Cx<T> *__restrict__ rows, const double *__restrict__ sym0,
+                         const T *__restrict__ symc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
@@ -102,14 +117,14 @@ __global__ void k_yscale(int Mt, int ns, int kfirst, int count, FftDesc d, const
     const int s = blockIdx.x / nkc, kx0 = (blockIdx.x % nkc) * xb;
     Cx<T> *slab = rows + (size_t)s * Mt * ns;
     for (int e = threadIdx.x; e < ns * xb; e += blockDim.x) {
-        const int y = e / xb, p = e % xb, kx = kx0 + p;
+        const int y = fdiv(e, fxb), p = e - y * xb, kx = kx0 + p;
         a[e] = (y < Mt && kx < ns) ? slab[(size_t)y * ns + kx] : cx<T>((T)0, (T)0);
     }
     __syncthreads();
-    Cx<T> *res = fft_smem<T>(a, b, d, xb, 1, xb, tw, -1);
+    Cx<T> *res = fft_smem<T>(a, b, d, xb, fxb, 1, xb, tw, -1);
     Cx<T> *oth = res == a ? b : a;
     for (int e = threadIdx.x; e < ns * xb; e += blockDim.x) {
-        const int ky = e / xb, p = e % xb, kx = kx0 + p;
+        const int ky = fdiv(e, fxb), p = e - ky * xb, kx = kx0 + p;
         T S = (T)0;
         if (kx < ns) {
             if (CLASS0) S = (T)sym0[(size_t)ky * ns + kx];
@@ -118,9 +133,9 @@ __global__ void k_yscale(int Mt, int ns, int kfirst, int count, FftDesc d, const
         res[e] = scale(res[e], S);
     }
     __syncthreads();
-    res = fft_smem<T>(res, oth, d, xb, 1, xb, tw, +1);
+    res = fft_smem<T>(res, oth, d, xb, fxb, 1, xb, tw, +1);
     for (int e = threadIdx.x; e < Mt * xb; e += blockDim.x) {
-        const int y = e / xb, p = e % xb, kx = kx0 + p;
+        const int y = fdiv(e, fxb), p = e - y * xb, kx = kx0 + p;
         if (kx < ns) slab[(size_t)y * ns + kx] = res[e];
     }
 }
@@ -128,22 +143,23 @@ __global__ void k_yscale(int Mt, int ns, int kfirst, int count, FftDesc d, const
 // ---- x inverse: CTA = rb rows; inverse FFT along x, keep the first Mt points
 template <typename T, bool TO_SLAB0>
 __global__ void k_xinv(int Mt, int ns, int kfirst, int nrows, FftDesc d, const Tw<T> *__restrict__ tw, int rb,
-                       const Cx<T> *__restrict__ rows, Cx<T> *__restrict__ zspec, double *__restrict__ slab0)
+                       FastDiv frb, FastDiv fns, FastDiv fMt, const Cx<T> *__restrict__ rows,
+                       Cx<T> *__restrict__ zspec, double *__restrict__ slab0)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
     Cx<T> *b = a + (size_t)rb * ns;
     const int r0 = blockIdx.x * rb;
     for (int e = threadIdx.x; e < rb * ns; e += blockDim.x) {
-        const int p = e / ns, r = r0 + p;
-        a[e] = r < nrows ? rows[(size_t)r * ns + (e % ns)] : cx<T>((T)0, (T)0);
+        const int p = fdiv(e, fns), r = r0 + p;
+        a[e] = r < nrows ? rows[(size_t)r * ns + (e - p * ns)] : cx<T>((T)0, (T)0);
     }
     __syncthreads();
-    Cx<T> *res = fft_smem<T>(a, b, d, rb, ns, 1, tw, +1);
+    Cx<T> *res = fft_smem<T>(a, b, d, rb, frb, ns, 1, tw, +1);
     for (int e = threadIdx.x; e < rb * Mt; e += blockDim.x) {
-        const int p = e / Mt, x = e % Mt, r = r0 + p;
+        const int p = fdiv(e, fMt), x = e - p * Mt, r = r0 + p;
         if (r >= nrows) continue;
-        const int s = r / Mt, y = r % Mt;
+        const int s = fdiv(r, fMt), y = r - s * Mt;
         const Cx<T> v = res[p * ns + x];
         if (TO_SLAB0) slab0[(size_t)y * Mt + x] = (double)v.re;
         else zspec[((size_t)(kfirst + s) * Mt + y) * Mt + x] = v;
@@ -152,7 +168,7 @@ __global__ void k_xinv(int Mt, int ns, int kfirst, int nrows, FftDesc d, const T
 
 // ---- z inverse: Hermitian completion along z, inverse FFT, real part
 template <typename T>
-__global__ void k_zinv(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restrict__ tw, int xb,
+__global__ void k_zinv(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restrict__ tw, int xb, FastDiv fxb,
                        const Cx<T> *__restrict__ zspec, const double *__restrict__ slab0, T *__restrict__ grid)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -161,7 +177,7 @@ __global__ void k_zinv(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restric
     const int nxc = (Mt + xb - 1) / xb;
     const int y = blockIdx.x / nxc, x0 = (blockIdx.x % nxc) * xb;
     for (int e = threadIdx.x; e < M3 * xb; e += blockDim.x) {
-        const int k = e / xb, p = e % xb, x = x0 + p;
+        const int k = fdiv(e, fxb), p = e - k * xb, x = x0 + p;
         Cx<T> v = cx<T>((T)0, (T)0);
         if (x < Mt) {
             if (k == 0) {
@@ -176,9 +192,9 @@ __global__ void k_zinv(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restric
         a[e] = v;
     }
     __syncthreads();
-    Cx<T> *res = fft_smem<T>(a, b, d, xb, 1, xb, tw, +1);
+    Cx<T> *res = fft_smem<T>(a, b, d, xb, fxb, 1, xb, tw, +1);
     for (int e = threadIdx.x; e < M3 * xb; e += blockDim.x) {
-        const int z = e / xb, p = e % xb, x = x0 + p;
+        const int z = fdiv(e, fxb), p = e - z * xb, x = x0 + p;
         if (x < Mt) grid[((size_t)z * Mt + y) * Mt + x] = res[e].re;
     }
 }
@@ -287,8 +303,8 @@ template <typename T> void launch_fourier(se1p_plan *p, cudaStream_t s)
         const int xb = p->xb_z;
         const int nxc = (Mt + xb - 1) / xb;
         const size_t sm = 2 * (size_t)M3 * xb * cbytes<T>();
-        k_zfwd<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb, (const T *)p->b.grid,
-                                            (Cx<T> *)p->b.zspec, p->b.slab0_in);
+        k_zfwd<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb, make_fastdiv(xb),
+                                            (const T *)p->b.grid, (Cx<T> *)p->b.zspec, p->b.slab0_in);
     }
     // the three slab classes are independent between the z passes: classes 0 (k3 = 0, FP64)
     // and 1 (set I) run on the plan's two Fourier streams, class 2 (set J) on s
@@ -296,34 +312,37 @@ template <typename T> void launch_fourier(se1p_plan *p, cudaStream_t s)
     cudaStreamWaitEvent(p->s_f[0], p->ev_f[0], 0);
     cudaStreamWaitEvent(p->s_f[1], p->ev_f[0], 0);
     const cudaStream_t s_main = s;
+    const FastDiv fMt = make_fastdiv(Mt);
     for (int c = 0; c < 3; ++c) {
         const SlabClass &C = p->cls[c];
         if (C.count == 0) continue;
         const cudaStream_t s = c == 2 ? s_main : p->s_f[c];  // this class's stream
         const int nrows = C.count * Mt;
+        const FastDiv frb = make_fastdiv(C.rb), fns = make_fastdiv(C.ns), fxb = make_fastdiv(C.xb);
         if (c == 0) {
             const size_t smx = 2 * (size_t)C.rb * C.ns * cbytes<double>();
             k_xfwd<double, true><<<(nrows + C.rb - 1) / C.rb, 256, smx, s>>>(
-                Mt, C.ns, 0, nrows, C.fd, (const Tw<double> *)C.tw, C.rb, nullptr, p->b.slab0_in, (Cx<double> *)C.rows);
+                Mt, C.ns, 0, nrows, C.fd, (const Tw<double> *)C.tw, C.rb, frb, fns, fMt, nullptr, p->b.slab0_in,
+                (Cx<double> *)C.rows);
             const int nkc = (C.ns + C.xb - 1) / C.xb;
             const size_t smy = 2 * (size_t)C.ns * C.xb * cbytes<double>();
             k_yscale<double, true><<<C.count * nkc, 256, smy, s>>>(Mt, C.ns, 0, C.count, C.fd, (const Tw<double> *)C.tw,
-                                                                  C.xb, (Cx<double> *)C.rows, p->b.sym0, nullptr);
+                                                                  C.xb, fxb, (Cx<double> *)C.rows, p->b.sym0, nullptr);
             k_xinv<double, true><<<(nrows + C.rb - 1) / C.rb, 256, smx, s>>>(
-                Mt, C.ns, 0, nrows, C.fd, (const Tw<double> *)C.tw, C.rb, (const Cx<double> *)C.rows, nullptr,
-                p->b.slab0_out);
+                Mt, C.ns, 0, nrows, C.fd, (const Tw<double> *)C.tw, C.rb, frb, fns, fMt, (const Cx<double> *)C.rows,
+                nullptr, p->b.slab0_out);
         } else {
             const size_t smx = 2 * (size_t)C.rb * C.ns * cbytes<T>();
             k_xfwd<T, false><<<(nrows + C.rb - 1) / C.rb, 256, smx, s>>>(
-                Mt, C.ns, C.kfirst, nrows, C.fd, (const Tw<T> *)C.tw, C.rb, (const Cx<T> *)p->b.zspec, nullptr,
-                (Cx<T> *)C.rows);
+                Mt, C.ns, C.kfirst, nrows, C.fd, (const Tw<T> *)C.tw, C.rb, frb, fns, fMt, (const Cx<T> *)p->b.zspec,
+                nullptr, (Cx<T> *)C.rows);
             const int nkc = (C.ns + C.xb - 1) / C.xb;
             const size_t smy = 2 * (size_t)C.ns * C.xb * cbytes<T>();
             k_yscale<T, false><<<C.count * nkc, 256, smy, s>>>(Mt, C.ns, C.kfirst, C.count, C.fd, (const Tw<T> *)C.tw,
-                                                              C.xb, (Cx<T> *)C.rows, nullptr, (const T *)C.sym);
+                                                              C.xb, fxb, (Cx<T> *)C.rows, nullptr, (const T *)C.sym);
             k_xinv<T, false><<<(nrows + C.rb - 1) / C.rb, 256, smx, s>>>(
-                Mt, C.ns, C.kfirst, nrows, C.fd, (const Tw<T> *)C.tw, C.rb, (const Cx<T> *)C.rows, (Cx<T> *)p->b.zspec,
-                nullptr);
+                Mt, C.ns, C.kfirst, nrows, C.fd, (const Tw<T> *)C.tw, C.rb, frb, fns, fMt, (const Cx<T> *)C.rows,
+                (Cx<T> *)p->b.zspec, nullptr);
         }
     }
     cudaEventRecord(p->ev_f[1], p->s_f[0]);
@@ -335,7 +354,7 @@ template <typename T> void launch_fourier(se1p_plan *p, cudaStream_t s)
         const int xb = p->xb_z;
         const int nxc = (Mt + xb - 1) / xb;
         const size_t sm = 2 * (size_t)M3 * xb * cbytes<T>();
-        k_zinv<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb,
+        k_zinv<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb, make_fastdiv(xb),
                                             (const Cx<T> *)p->b.zspec, p->b.slab0_out, (T *)p->b.grid);
     }
 }

@@ -138,10 +138,35 @@ template <typename T> __device__ __forceinline__ Cx<T> tw_mul(Cx<T> v, Tw<T> w, 
 // ------------------------------------------------------------------ FFT descriptor
 // A length-n transform factored into radices (applied first to last).  The
 // twiddle table holds w^t = exp(-2 pi i t / n), t = 0..n-1.
+// Exact floor(x / d) for 0 <= x < 2^31 and 1 <= d < 2^31 with one multiply-high, an add and a
+// shift: the round-up method of Granlund and Montgomery (Division by invariant integers using
+// multiplication, PLDI 1994), l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// q = (umulhi(m, x) + x) >> l.  Built on the host for divisors known at plan creation, so that
+// index arithmetic in the hot loops avoids the integer division sequence.
+struct FastDiv {
+    unsigned d = 1, m = 1, l = 0;
+};
+inline FastDiv make_fastdiv(unsigned d)
+{
+    FastDiv f;
+    f.d = d;
+    f.l = 0;
+    while ((1ull << f.l) < d) ++f.l;
+    f.m = (unsigned)(((1ull << 32) * ((1ull << f.l) - d)) / d + 1);
+    return f;
+}
+__device__ __forceinline__ int fdiv(int x, const FastDiv &f)
+{
+    return (int)((__umulhi((unsigned)x, f.m) + (unsigned)x) >> f.l);
+}
+
+// Mixed-radix plan of one FFT length: radices in pass order, and per pass the dividers of the
+// butterfly span Ns (product of the earlier radices) and of the butterfly count n / R.
 struct FftDesc {
     int n;
     int nrad;
     int rad[24];
+    FastDiv ns[24], nb[24];
 };
 
 // Small DFTs, X_k = sum_j a_j exp(s 2 pi i j k / R), s = -1 forward, +1 inverse.
@@ -236,8 +261,8 @@ template <typename T, int R> __device__ __forceinline__ void dft_odd(Cx<T> *v, i
 // memory: element j of pencil p lives at buf[p * sp + j * sj].
 template <typename T, int R>
 __device__ __forceinline__ void stockham_pass(const Cx<T> *__restrict__ src, Cx<T> *__restrict__ dst, int n,
-                                              int Ns, int npen, int sp, int sj,
-                                              const Tw<T> *__restrict__ tw, int s)
+                                              int Ns, const FastDiv &fns, const FastDiv &fnb, const FastDiv &fpen,
+                                              int npen, int sp, int sj, const Tw<T> *__restrict__ tw, int s)
 {
     const int nb = n / R;
     const int total = nb * npen;
@@ -245,13 +270,13 @@ __device__ __forceinline__ void stockham_pass(const Cx<T> *__restrict__ src, Cx<
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         int i, p;
         if (sj == 1) {
-            i = idx % nb;
-            p = idx / nb;
+            p = fdiv(idx, fnb);
+            i = idx - p * nb;
         } else {
-            p = idx % npen;
-            i = idx / npen;
+            i = fdiv(idx, fpen);
+            p = idx - i * npen;
         }
-        const int k = i % Ns;
+        const int q = fdiv(i, fns), k = i - q * Ns;
         Cx<T> v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = src[p * sp + (i + r * nb) * sj];
@@ -263,7 +288,7 @@ __device__ __forceinline__ void stockham_pass(const Cx<T> *__restrict__ src, Cx<
         else if constexpr (R == 4) dft4(v, s);
         else if constexpr (R == 8) dft8(v, s);
         else dft_odd<T, R>(v, s);
-        const int base = (i / Ns) * Ns * R + k;
+        const int base = q * Ns * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) dst[p * sp + (base + r * Ns) * sj] = v[r];
     }
@@ -271,21 +296,22 @@ __device__ __forceinline__ void stockham_pass(const Cx<T> *__restrict__ src, Cx<
 
 // Batched in-shared-memory FFT (unnormalised; s = -1 forward, +1 inverse).
 // a holds the input, b is scratch of the same shape; returns the buffer that
-// holds the result.  Must be called by all threads of the block.
+// holds the result.  Must be called by all threads of the block.  fpen divides by npen.
 template <typename T>
-__device__ Cx<T> *fft_smem(Cx<T> *a, Cx<T> *b, const FftDesc &d, int npen, int sp, int sj,
+__device__ Cx<T> *fft_smem(Cx<T> *a, Cx<T> *b, const FftDesc &d, int npen, const FastDiv &fpen, int sp, int sj,
                            const Tw<T> *__restrict__ tw, int s)
 {
     int Ns = 1;
     for (int st = 0; st < d.nrad; ++st) {
         const int R = d.rad[st];
+        const FastDiv &fns = d.ns[st], &fnb = d.nb[st];
         switch (R) {
-        case 2: stockham_pass<T, 2>(a, b, d.n, Ns, npen, sp, sj, tw, s); break;
-        case 3: stockham_pass<T, 3>(a, b, d.n, Ns, npen, sp, sj, tw, s); break;
-        case 4: stockham_pass<T, 4>(a, b, d.n, Ns, npen, sp, sj, tw, s); break;
-        case 5: stockham_pass<T, 5>(a, b, d.n, Ns, npen, sp, sj, tw, s); break;
-        case 7: stockham_pass<T, 7>(a, b, d.n, Ns, npen, sp, sj, tw, s); break;
-        default: stockham_pass<T, 8>(a, b, d.n, Ns, npen, sp, sj, tw, s); break;
+        case 2: stockham_pass<T, 2>(a, b, d.n, Ns, fns, fnb, fpen, npen, sp, sj, tw, s); break;
+        case 3: stockham_pass<T, 3>(a, b, d.n, Ns, fns, fnb, fpen, npen, sp, sj, tw, s); break;
+        case 4: stockham_pass<T, 4>(a, b, d.n, Ns, fns, fnb, fpen, npen, sp, sj, tw, s); break;
+        case 5: stockham_pass<T, 5>(a, b, d.n, Ns, fns, fnb, fpen, npen, sp, sj, tw, s); break;
+        case 7: stockham_pass<T, 7>(a, b, d.n, Ns, fns, fnb, fpen, npen, sp, sj, tw, s); break;
+        default: stockham_pass<T, 8>(a, b, d.n, Ns, fns, fnb, fpen, npen, sp, sj, tw, s); break;
         }
         __syncthreads();
         Cx<T> *t = a;

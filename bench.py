@@ -235,6 +235,60 @@ def roofline(stage_ms, n_evals, info, n, precision, peaks, clock_mhz, workload_n
                 frac=byts / t / 1e9 / peaks["hbm_gbs"], traffic=None, algorithmic="64 B/particle", stage_ms=per)
 
 
+def fourier_bytes(info, word):
+    """Bytes the Fourier passes must read and write per evaluation: the z passes read or write the
+    real grid and the k3 > 0 spectra, each slab-class pass reads its input rows and writes its output
+    rows (Mt of the ns padded rows, the padding lives in shared memory), the y pass reads its symbol;
+    the k3 = 0 class is FP64 throughout."""
+    Mt, M3, n0, nI, nIm = info["Mt"], info["M3"], info["n0"], info["nI"], info["n_I_modes"]
+    K3 = M3 // 2 + 1
+    cw = 2 * word
+    b = M3 * Mt * Mt * word + (K3 - 1) * Mt * Mt * cw + Mt * Mt * 8             # z forward
+    b += Mt * Mt * 8 + 4 * Mt * n0 * 16 + n0 * n0 * 8 + Mt * Mt * 8               # class 0 (k3 = 0)
+    for cnt, ns in ((nIm, nI), (K3 - 1 - nIm, Mt)):                                # classes I and J
+        b += cnt * (Mt * Mt * cw + 4 * Mt * ns * cw + ns * ns * word + Mt * Mt * cw)
+    b += (K3 - 1) * Mt * Mt * cw + Mt * Mt * 8 + M3 * Mt * Mt * word              # z inverse
+    return b
+
+
+def stage_rooflines(stage_ms, n_evals, info, n, precision, peaks, P, pairs):
+    """Each stage of the evaluation against its own bound, from times taken with the stages run in
+    sequence (profiling mode 2): spread and gather against the FP32 (FP64) FMA peak, the real space
+    at 40 flop per pair, the Fourier passes and the particle bookkeeping against HBM."""
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu = NUM_SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12 if precision == "mixed" else 1.25
+    hbm = peaks["hbm_gbs"]
+    word = 4 if precision == "mixed" else 8
+    rec = 32 if precision == "mixed" else 48
+    cell = 32 if precision == "mixed" else 64
+    work = {
+        "pack": ("hbm", n * (32 + 2 * 32 + 2 * 8 + rec + 3 * P * word + cell), "x, q in; sorted records, "
+                 "keys and window tables out"),
+        "spread": ("alu", n * 2.0 * P ** 3, f"{2 * P ** 3} flop/particle (one FMA per support point)"),
+        "fourier": ("hbm", fourier_bytes(info, word), "read + write of every pass"),
+        "gather": ("alu", n * 4.0 * P ** 3, f"{4 * P ** 3} flop/particle (phi and x-derivative chains)"),
+        "real": ("alu", pairs * 40.0, "40 flop/pair inside rc"),
+        "final": ("hbm", n * (2 * 32 + 32 + 8), "internal phi, F in; caller-order phi, F out"),
+    }
+    out = {}
+    for k, t in stage_ms.items():
+        if k not in work or n_evals <= 0:
+            continue
+        sec = t / n_evals * 1e-3
+        bound, amount, what = work[k]
+        if sec <= 0:
+            continue
+        if bound == "alu":
+            a = amount / sec / 1e12
+            out[k] = {"ms": sec * 1e3, "bound": "alu", "achieved": a, "peak": alu, "unit": "TFLOP/s",
+                      "frac": a / alu, "algorithmic": what}
+        else:
+            a = amount / sec / 1e9
+            out[k] = {"ms": sec * 1e3, "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
+                      "frac": a / hbm, "algorithmic": what}
+    return out
+
+
 def kernels_per_eval(info, real_space):
     """Kernels one se1p_eval launches: pack, scan, scatter, spread, z forward, three passes
     per active slab class, z inverse, gather, real space, finalize, energy."""
@@ -349,6 +403,12 @@ def run_gpu(args, rank, world, local_rank):
     if st != 0:
         raise RuntimeError(f"device status {se1p.STATUS.get(st)}")
     total_ms = max_over_ranks(total_ms, dist, "cuda")
+    # each stage alone (untimed for the metric): profiling mode 2 runs the stages in sequence
+    se1p.se1p_plan_set_profiling(plan.handle, 2)
+    for _ in range(min(args.steps, 20)):
+        step()
+    alone_ms, alone_n = se1p.se1p_plan_stage_times(plan.handle)
+    se1p.se1p_plan_set_profiling(plan.handle, False)
 
     # end to end through the host entry point: pinned host buffers, H2D + eval + D2H each step
     xh = torch.as_tensor(sys_.x).contiguous().pin_memory()
@@ -394,6 +454,8 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": int(launches_per_eval * args.steps),
         "clocks": clocks,
         "accuracy": acc,
+        "stages_alone": stage_rooflines(alone_ms, alone_n, info, n, args.precision, peaks, p["P"],
+                                        n * info["density"] * 4.0 / 3.0 * math.pi * p["rc"] ** 3),
     }
     if not args.no_extras:
         out["fp64"] = measure_fp64(sys_, p, n, x, q, stream, min(args.steps, 20))

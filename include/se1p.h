@@ -177,8 +177,11 @@ typedef enum {
 } se1p_stage;
 
 /* Enable (1) or disable (0) per-stage event recording for subsequent se1p_eval
- * calls (at most 4096 evaluations are kept).  Enabling clears earlier records.
- * Synchronous. */
+ * calls (at most 4096 evaluations are kept).  With 2, recording is on and the
+ * evaluation runs its stages one after another on the caller's stream instead of
+ * overlapping the real space with the grid path, so that each stage's time is
+ * its time alone (same results).  Enabling clears earlier records.  Synchronous.
+ * Other values: SE1P_ERR_INVALID_ARG. */
 se1p_status se1p_plan_set_profiling(se1p_plan *plan, int enable);
 
 /* Synchronise the device and return, per stage, the summed elapsed milliseconds

@@ -277,8 +277,9 @@ se1p_status run_eval(se1p_plan *p, int n, const double *x, const double *q, doub
                      double *energy, cudaStream_t s)
 {
     StageMarks m(p);
-    // the real space writes phi2 / frc2 (free outside the adjoint) and the finalisation adds them
-    const bool real = p->geo.rc > 0;
+    // the real space writes phi2 / frc2 (free outside the adjoint) and the finalisation adds them;
+    // profiling mode 2 runs it in sequence with the grid path instead
+    const bool real = p->geo.rc > 0 && p->profiling != 2;
     run_pass<T>(p, n, x, q, p->b.phi_int, p->b.frc_int, 0, 1, s, &m, real ? p->b.phi2 : nullptr,
                 real ? p->b.frc2 : nullptr);
     m.begin(SE1P_STAGE_FINAL, s);
@@ -539,7 +540,7 @@ se1p_status se1p_eval(se1p_plan *p, int n, const double *x, const double *q, dou
 
 se1p_status se1p_plan_set_profiling(se1p_plan *p, int enable)
 {
-    if (!p) return SE1P_ERR_INVALID_ARG;
+    if (!p || enable < 0 || enable > 2) return SE1P_ERR_INVALID_ARG;
     if (cudaDeviceSynchronize() != cudaSuccess) return SE1P_ERR_CUDA;
     destroy_events(p);
     p->profiling = 0;
@@ -553,7 +554,7 @@ se1p_status se1p_plan_set_profiling(se1p_plan *p, int enable)
             return SE1P_ERR_CUDA;
         }
     }
-    p->profiling = 1;
+    p->profiling = enable;
     return SE1P_OK;
 }
 

@@ -205,8 +205,9 @@ def se1p_real_space(plan, n, x, q, phi=None, force=None, stream=None) -> None:
            "se1p_real_space")
 
 
-def se1p_plan_set_profiling(plan, enable: bool) -> None:
-    _check(load().se1p_plan_set_profiling(plan, int(bool(enable))), "se1p_plan_set_profiling")
+def se1p_plan_set_profiling(plan, enable) -> None:
+    """enable: False/0 off, True/1 on, 2 on with the stages run in sequence (times alone)."""
+    _check(load().se1p_plan_set_profiling(plan, int(enable)), "se1p_plan_set_profiling")
 
 
 def se1p_plan_stage_times(plan) -> tuple[dict, int]:

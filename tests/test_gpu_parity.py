@@ -252,3 +252,27 @@ def test_back_to_back_evaluations_on_one_plan(precision):
         assert max_rel(phi.cpu().numpy(), ref.phi.cpu().numpy()) < tol
         assert max_rel(F.cpu().numpy(), ref.force.cpu().numpy()) < tol
         assert E.item() == pytest.approx(ref.energy.item(), rel=tol)
+
+
+@pytest.mark.parametrize("precision", [se1p.SE1P_FP64, se1p.SE1P_MIXED])
+def test_profiling_modes_give_the_same_results(precision):
+    """Profiling mode 2 runs the stages in sequence (the real space after the gather, adding into
+    the same outputs) instead of overlapping them: the results equal the overlapped evaluation's up
+    to the order of the atomic additions, and every stage is recorded."""
+    x, q, prm = CASES["cubic_P24"]
+    plan = make_plan(prm, len(q), precision=precision)
+    xd, qd = dev(x), dev(q)
+    ref = plan.eval(xd, qd)
+    tol = 1e-12 if precision == se1p.SE1P_FP64 else 1e-6
+    for mode in (1, 2):
+        se1p.se1p_plan_set_profiling(plan.handle, mode)
+        r = plan.eval(xd, qd)
+        ms, ne = se1p.se1p_plan_stage_times(plan.handle)
+        assert ne == 1 and all(v > 0 for v in ms.values())
+        assert max_rel(r.phi.cpu().numpy(), ref.phi.cpu().numpy()) < tol
+        assert max_rel(r.force.cpu().numpy(), ref.force.cpu().numpy()) < tol
+        assert r.energy.item() == pytest.approx(ref.energy.item(), rel=tol)
+    se1p.se1p_plan_set_profiling(plan.handle, 0)
+    with pytest.raises(se1p.SE1PError):
+        se1p.se1p_plan_set_profiling(plan.handle, 3)
+    plan.close()

@@ -152,3 +152,42 @@ def test_charges_on_grid_nodes(P):
     plan.close()
     assert np.max(np.abs(phi - phi_ref)) < 1e-10 * np.max(np.abs(phi_ref))
     assert np.max(np.abs(F - F_ref)) < 1e-10 * np.max(np.abs(F_ref))
+
+
+@pytest.mark.parametrize("precision", [se1p.SE1P_FP64, se1p.SE1P_MIXED])
+def test_random_configurations_in_one_batch(precision):
+    """The random configurations above as one batch (one captured graph over plans that differ in
+    box, P, grid, padding, class split and rc): every system's phi, F and U against the restatement
+    of Algorithm 1 plus the direct real-space and self terms (FP64 element by element; mixed at the
+    mixed path's tolerance, for systems with eta < 1)."""
+    seeds = [0, 2, 4, 6, 9, 11, 101, 103, 104]
+    cases = [draw(s) for s in seeds]
+    params = [se1p.make_params(prm["L"], prm["xi"], prm["M"], prm["P"], Mt=prm["Mt"], n0=prm["n0"], nI=prm["nI"],
+                               nl=prm["nl"], rc=prm["rc"], precision=precision) for _, _, prm in cases]
+    ns = [len(q) for _, q, _ in cases]
+    offsets = np.concatenate([[0], np.cumsum(ns)]).astype(int)
+    x = torch.as_tensor(np.concatenate([c[0] for c in cases]), device="cuda").contiguous()
+    q = torch.as_tensor(np.concatenate([c[1] for c in cases]), device="cuda").contiguous()
+    ntot = int(offsets[-1])
+    phi = torch.empty(ntot, dtype=torch.float64, device="cuda")
+    F = torch.empty((ntot, 3), dtype=torch.float64, device="cuda")
+    E = torch.empty(len(cases), dtype=torch.float64, device="cuda")
+    b = se1p.se1p_batch_create(params, ns)
+    se1p.se1p_batch_eval(b, offsets, x, q, phi, F, E)
+    assert se1p.se1p_batch_sync_status(b) == 0
+    se1p.se1p_batch_destroy(b)
+    phi, F, E = phi.cpu().numpy(), F.cpu().numpy(), E.cpu().numpy()
+    rel = lambda a, c: np.sqrt(np.sum((a - c) ** 2) / np.sum(c ** 2))
+    for i, (xs, qs, prm) in enumerate(cases):
+        a, c = offsets[i], offsets[i + 1]
+        phi_ref, F_ref = reference_parts(xs, qs, prm)
+        U_ref = 0.5 * float(qs @ phi_ref)
+        if precision == se1p.SE1P_FP64:
+            assert np.max(np.abs(phi[a:c] - phi_ref)) < 1e-9 * np.max(np.abs(phi_ref)), prm
+            assert np.max(np.abs(F[a:c] - F_ref)) < 1e-9 * np.max(np.abs(F_ref)), prm
+            assert abs(E[i] - U_ref) < 1e-9 * float(np.abs(qs) @ np.abs(phi_ref)), prm
+        else:
+            eta = prm["P"] * prm["xi"] ** 2 * (prm["L"][0] / prm["M"][0]) ** 2 / (0.95 ** 2 * np.pi)
+            if eta < 1.0:
+                assert rel(phi[a:c], phi_ref) < 1e-5, prm
+                assert rel(F[a:c], F_ref) < 1e-5, prm

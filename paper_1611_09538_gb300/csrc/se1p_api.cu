@@ -139,11 +139,8 @@ template <typename T> std::vector<Tw<T>> twiddles(int n)
     return w;
 }
 
-int signed_idx(int i, int n) { return i <= (n - 1) / 2 ? i : i - n; }
-
 template <typename T> se1p_status build_tables(se1p_plan *p, Alloc &A)
 {
-    const Geo &g = p->geo;
     // twiddles
     p->b.tw_z = A.dev(sizeof(Tw<T>) * p->M3);
     for (int c = 0; c < 3; ++c) {

@@ -134,7 +134,7 @@ __global__ void k_na_scatter(Geo g, int n, const double *__restrict__ xyzq, cons
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double4 p = reinterpret_cast<const double4 *>(xyzq)[i];
+    const double4_32a p = reinterpret_cast<const double4_32a *>(xyzq)[i];  // 32-byte records
     const int cell = key[i];
     const int pos = atomicAdd(cursor + cell, 1);
     CellRec<T> c;

@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(Geo g, int n, const
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     int pos = -1;
     if (i < n) {
-        const double4 p = reinterpret_cast<const double4 *>(xyzq)[i];
+        const double4_32a p = reinterpret_cast<const double4_32a *>(xyzq)[i];  // 32-byte records
         const Support s = particle_support(g, p.x, p.y, p.z);
         pos = atomicAdd(bin_cursor + bin_key[i], 1);
         PartRec<T> r;

@@ -444,7 +444,10 @@ se1p_status se1p_plan_create(const se1p_params *prm, int n_max, se1p_plan **out)
         while (v > 1 && (units + v - 1) / v < min_ctas) v >>= 1;
         return v;
     };
-    p->xb_z = shrink(pow2_fit(2 * (size_t)p->M3 * cT, 32), (long)p->Mt * p->Mt);
+    // z passes: a CTA holds xb_z complex pencils of M3 points (twice, for the Stockham passes); with Mt
+    // even each complex pencil carries two real ones
+    p->zpair = p->Mt % 2 == 0;
+    p->xb_z = shrink(pow2_fit(2 * (size_t)p->M3 * cT, 32), (long)p->Mt * p->Mt / (p->zpair ? 2 : 1));
     for (int c = 0; c < 3; ++c) {
         const size_t cc = c == 0 ? sizeof(Cx<double>) : cT;
         SlabClass &C = p->cls[c];

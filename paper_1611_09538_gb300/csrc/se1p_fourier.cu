@@ -74,6 +74,85 @@ __global__ void k_zfwd(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restric
     }
 }
 
+// ---- z forward on pencil pairs (Mt even): the real pencils 2j and 2j + 1 of a row form one complex
+// pencil H[2j] + i H[2j + 1] (one aligned two-element load); their spectra follow from its FFT Z by
+// Hermitian symmetry, X_2j[k] = (Z[k] + conj Z[-k]) / 2 and X_2j+1[k] = (Z[k] - conj Z[-k]) / 2i.
+// CTA = (y, chunk of xp pairs); half the FFT work and shared memory per real pencil.
+template <typename T> struct Pair2;
+template <> struct Pair2<float> { using type = float2; };
+template <> struct Pair2<double> { using type = double2; };
+
+template <typename T>
+__global__ void k_zfwd_pair(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restrict__ tw, int xp, FastDiv fxp,
+                            const T *__restrict__ grid, Cx<T> *__restrict__ zspec, double *__restrict__ slab0)
+{
+    using V2 = typename Pair2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
+    Cx<T> *b = a + (size_t)M3 * xp;
+    const int npair = Mt / 2, nxc = (npair + xp - 1) / xp;
+    const int y = blockIdx.x / nxc, j0 = (blockIdx.x % nxc) * xp;
+    for (int e = threadIdx.x; e < M3 * xp; e += blockDim.x) {
+        const int z = fdiv(e, fxp), pp = e - z * xp, j = j0 + pp;
+        Cx<T> v = cx<T>((T)0, (T)0);
+        if (j < npair) {
+            const V2 h = *reinterpret_cast<const V2 *>(grid + ((size_t)z * Mt + y) * Mt + 2 * j);
+            v = cx<T>(h.x, h.y);
+        }
+        a[e] = v;
+    }
+    __syncthreads();
+    // k3 = 0: each pencil's z sum to FP64 accuracy, as in k_zfwd (real part: pencil 2j, imaginary: 2j + 1)
+    {
+        __shared__ double part[2][256];
+        const int G = blockDim.x / xp;  // xp is a power of 2 <= 32 that divides blockDim (256)
+        const int g = threadIdx.x / xp, pp = threadIdx.x - g * xp;
+        double sre = 0.0, sim = 0.0;
+        if constexpr (sizeof(T) == sizeof(double)) {
+            for (int z = g; z < M3; z += G) {
+                sre += (double)a[z * xp + pp].re;
+                sim += (double)a[z * xp + pp].im;
+            }
+        } else {
+            float hr = 0.0f, lr = 0.0f, hi = 0.0f, li = 0.0f;
+            for (int z = g; z < M3; z += G) {
+                const Cx<float> v = a[z * xp + pp];
+                const float tr = hr + v.re, br = tr - hr;
+                lr += (hr - (tr - br)) + (v.re - br);
+                hr = tr;
+                const float ti = hi + v.im, bi = ti - hi;
+                li += (hi - (ti - bi)) + (v.im - bi);
+                hi = ti;
+            }
+            sre = (double)hr + (double)lr;
+            sim = (double)hi + (double)li;
+        }
+        part[0][threadIdx.x] = sre;
+        part[1][threadIdx.x] = sim;
+        __syncthreads();
+        if (g == 0 && j0 + pp < npair) {
+            double tr = 0.0, ti = 0.0;
+            for (int k = 0; k < G; ++k) {
+                tr += part[0][k * xp + pp];
+                ti += part[1][k * xp + pp];
+            }
+            slab0[(size_t)y * Mt + 2 * (j0 + pp)] = tr;
+            slab0[(size_t)y * Mt + 2 * (j0 + pp) + 1] = ti;
+        }
+    }
+    __syncthreads();
+    Cx<T> *res = fft_smem<T>(a, b, d, xp, fxp, 1, xp, tw, -1);
+    for (int e = threadIdx.x; e < (K3 - 1) * xp; e += blockDim.x) {
+        const int k1 = fdiv(e, fxp), pp = e - k1 * xp, k = 1 + k1, j = j0 + pp;
+        if (j < npair) {
+            const Cx<T> zk = res[k * xp + pp], zm = res[(M3 - k) * xp + pp];
+            Cx<T> *dst = zspec + ((size_t)k * Mt + y) * Mt + 2 * j;
+            dst[0] = cx<T>((zk.re + zm.re) * (T)0.5, (zk.im - zm.im) * (T)0.5);
+            dst[1] = cx<T>((zk.im + zm.im) * (T)0.5, (zm.re - zk.re) * (T)0.5);
+        }
+    }
+}
+
 // ---- x forward: CTA = rb rows (slab s, y) of one class; smem [row][ns]
 template <typename T, bool FROM_SLAB0>
 __global__ void k_xfwd(int Mt, int ns, int kfirst, int nrows, FftDesc d, const Tw<T> *__restrict__ tw, int rb,
@@ -199,6 +278,52 @@ __global__ void k_zinv(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restric
     }
 }
 
+// ---- z inverse on pencil pairs (Mt even): Z = X_2j + i X_2j+1 over the Hermitian-completed spectra;
+// the real and imaginary parts of its inverse FFT are the pencils 2j and 2j + 1
+template <typename T>
+__global__ void k_zinv_pair(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restrict__ tw, int xp, FastDiv fxp,
+                            const Cx<T> *__restrict__ zspec, const double *__restrict__ slab0, T *__restrict__ grid)
+{
+    using V2 = typename Pair2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
+    Cx<T> *b = a + (size_t)M3 * xp;
+    const int npair = Mt / 2, nxc = (npair + xp - 1) / xp;
+    const int y = blockIdx.x / nxc, j0 = (blockIdx.x % nxc) * xp;
+    for (int e = threadIdx.x; e < M3 * xp; e += blockDim.x) {
+        const int k = fdiv(e, fxp), pp = e - k * xp, j = j0 + pp;
+        Cx<T> v = cx<T>((T)0, (T)0);
+        if (j < npair) {
+            Cx<T> xe, xo;
+            if (k == 0) {
+                xe = cx<T>((T)slab0[(size_t)y * Mt + 2 * j], (T)0);
+                xo = cx<T>((T)slab0[(size_t)y * Mt + 2 * j + 1], (T)0);
+            } else if (k < K3) {
+                const Cx<T> *src = zspec + ((size_t)k * Mt + y) * Mt + 2 * j;
+                xe = src[0];
+                xo = src[1];
+            } else {
+                const Cx<T> *src = zspec + ((size_t)(M3 - k) * Mt + y) * Mt + 2 * j;
+                xe = cx<T>(src[0].re, -src[0].im);
+                xo = cx<T>(src[1].re, -src[1].im);
+            }
+            v = cx<T>(xe.re - xo.im, xe.im + xo.re);
+        }
+        a[e] = v;
+    }
+    __syncthreads();
+    Cx<T> *res = fft_smem<T>(a, b, d, xp, fxp, 1, xp, tw, +1);
+    for (int e = threadIdx.x; e < M3 * xp; e += blockDim.x) {
+        const int z = fdiv(e, fxp), pp = e - z * xp, j = j0 + pp;
+        if (j < npair) {
+            V2 o;
+            o.x = res[e].re;
+            o.y = res[e].im;
+            *reinterpret_cast<V2 *>(grid + ((size_t)z * Mt + y) * Mt + 2 * j) = o;
+        }
+    }
+}
+
 // ---- k3 = 0 scaling table in FP64 (Eqs. 3.5, 3.9-3.10), including 1/(n0^2 M3)
 __global__ void k_vico(int n0, double dkap, double R, double xi, double eta, double norm, double *__restrict__ sym)
 {
@@ -285,6 +410,8 @@ template <typename T> int configure_fourier_kernels(se1p_plan *p)
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaError_t e = cudaSuccess;
     e = (cudaError_t)(e | allow_max_dynamic_smem(k_zfwd<T>, maxsm));
+    e = (cudaError_t)(e | allow_max_dynamic_smem(k_zfwd_pair<T>, maxsm));
+    e = (cudaError_t)(e | allow_max_dynamic_smem(k_zinv_pair<T>, maxsm));
     e = (cudaError_t)(e | allow_max_dynamic_smem(k_zinv<T>, maxsm));
     e = (cudaError_t)(e | allow_max_dynamic_smem(k_xfwd<T, false>, maxsm));
     e = (cudaError_t)(e | allow_max_dynamic_smem(k_xinv<T, false>, maxsm));
@@ -301,10 +428,18 @@ template <typename T> void launch_fourier(se1p_plan *p, cudaStream_t s)
     // z forward
     {
         const int xb = p->xb_z;
-        const int nxc = (Mt + xb - 1) / xb;
         const size_t sm = 2 * (size_t)M3 * xb * cbytes<T>();
-        k_zfwd<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb, make_fastdiv(xb),
-                                            (const T *)p->b.grid, (Cx<T> *)p->b.zspec, p->b.slab0_in);
+        if (p->zpair) {  // xb pencil pairs per CTA
+            const int nxc = (Mt / 2 + xb - 1) / xb;
+            k_zfwd_pair<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb,
+                                                     make_fastdiv(xb), (const T *)p->b.grid, (Cx<T> *)p->b.zspec,
+                                                     p->b.slab0_in);
+        } else {
+            const int nxc = (Mt + xb - 1) / xb;
+            k_zfwd<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb,
+                                                make_fastdiv(xb), (const T *)p->b.grid, (Cx<T> *)p->b.zspec,
+                                                p->b.slab0_in);
+        }
     }
     // the three slab classes are independent between the z passes: classes 0 (k3 = 0, FP64)
     // and 1 (set I) run on the plan's two Fourier streams, class 2 (set J) on s
@@ -352,10 +487,18 @@ template <typename T> void launch_fourier(se1p_plan *p, cudaStream_t s)
     // z inverse
     {
         const int xb = p->xb_z;
-        const int nxc = (Mt + xb - 1) / xb;
         const size_t sm = 2 * (size_t)M3 * xb * cbytes<T>();
-        k_zinv<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb, make_fastdiv(xb),
-                                            (const Cx<T> *)p->b.zspec, p->b.slab0_out, (T *)p->b.grid);
+        if (p->zpair) {
+            const int nxc = (Mt / 2 + xb - 1) / xb;
+            k_zinv_pair<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb,
+                                                     make_fastdiv(xb), (const Cx<T> *)p->b.zspec, p->b.slab0_out,
+                                                     (T *)p->b.grid);
+        } else {
+            const int nxc = (Mt + xb - 1) / xb;
+            k_zinv<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb,
+                                                make_fastdiv(xb), (const Cx<T> *)p->b.zspec, p->b.slab0_out,
+                                                (T *)p->b.grid);
+        }
     }
 }
 

@@ -63,7 +63,8 @@ struct se1p_plan {
     int device = 0;
     int Mt = 0, M3 = 0, K3 = 0, n0 = 0, nI = 0, nl = 0;
     se1p::FftDesc fd_z{};
-    int xb_z = 1;
+    int xb_z = 1;      // z passes: pencils per CTA, or pencil pairs per CTA when zpair
+    bool zpair = false;  // Mt even: the z passes transform two real pencils as one complex pencil
     se1p::SlabClass cls[3];  // 0: k3 = 0 (FP64 always), 1: I, 2: J
     se1p::Buffers b;
     std::vector<void *> dev_allocs;

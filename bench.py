@@ -291,10 +291,13 @@ def stage_rooflines(stage_ms, n_evals, info, n, precision, peaks, P, pairs):
 
 def kernels_per_eval(info, real_space):
     """Kernels one se1p_eval launches: pack, scan, scatter, spread, z forward, three passes
-    per active slab class, z inverse, gather, real space, finalize, energy."""
+    per active slab class, z inverse, gather, real space, finalize, energy; above 65 536
+    real-space cells the cell histogram takes a three-kernel multi-block scan as well."""
     k3 = info["M3"] // 2 + 1
     classes = 1 + (info["n_I_modes"] > 0) + (k3 - 1 - info["n_I_modes"] > 0)
-    return 4 + 1 + 3 * classes + 1 + 1 + (1 if real_space else 0) + 2
+    ncells = info["cells"][0] * info["cells"][1] * info["cells"][2]
+    scan = 3 if real_space and ncells > 16 * 4096 else 0
+    return 4 + 1 + 3 * classes + 1 + 1 + (1 if real_space else 0) + 2 + scan
 
 
 # ------------------------------------------------------------------ multi-rank bookkeeping

@@ -11,7 +11,12 @@ namespace se1p {
 namespace {
 
 constexpr int kRealWarps = 4;  // warps per CTA (warps work independently)
-constexpr int kRealSplit = 2;  // warps sharing one group of targets (source rows split between them)
+// Warps sharing one group of targets (SPLIT, a template parameter: the source rows are split
+// between them and FP64 atomics combine their sums).  Four pay where a target has many neighbours,
+// two where the grid path dominates; measured beside the grid path: N = 10^5 in the unit box,
+// rc = 0.15 (~1400 expected neighbours): 1.528 ms with four, 1.543 with two; N = 10^6 in [1,1,8],
+// rc = 0.09 (~380): 12.42 ms with four, 12.32 with two.
+constexpr double kRealSplitNeighbours = 800.0;
 constexpr int kCand = 96;      // per-warp candidate list (flushed at >= 64)
 constexpr int kRealTargets = 16;                     // targets per warp
 constexpr int kLanesPerTarget = 32 / kRealTargets;   // lanes sharing a target (alternate candidates)
@@ -139,7 +144,7 @@ __device__ __forceinline__ void pair_terms(T dx, T dy, T dz, T qs, T rc2, T xi, 
 //            r <= rc test and the pair terms, branch-free.
 // (Spreading the marks of busy lanes over idle ones through shared memory was
 // measured slower: the bookkeeping per pair costs more than the idle lanes.)
-template <typename T>
+template <typename T, int SPLIT>
 __global__ void __launch_bounds__(32 * kRealWarps) k_real(Geo g, int n, const int *__restrict__ cell_start,
                                                           const CellRec<T> *__restrict__ cells,
                                                           const int *__restrict__ cell_key,
@@ -150,7 +155,7 @@ __global__ void __launch_bounds__(32 * kRealWarps) k_real(Geo g, int n, const in
     __shared__ float4 cposd[sizeof(T) == 4 ? 1 : kRealWarps][sizeof(T) == 4 ? 1 : kCand];  // FP64: float copy
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * kRealWarps + wib;
-    const int warp = gw / kRealSplit, part = gw % kRealSplit;  // target group, share of the source rows
+    const int warp = gw / SPLIT, part = gw % SPLIT;  // target group, share of the source rows
     const int half = lane / kRealTargets;  // which share of the candidates this lane takes
     const int t = warp * kRealTargets + lane % kRealTargets;
     if (warp * kRealTargets >= n) return;  // whole warp beyond the particles
@@ -260,7 +265,7 @@ __global__ void __launch_bounds__(32 * kRealWarps) k_real(Geo g, int n, const in
 
     const int nyr = ny_hi - ny_lo + 1;
     const int nrows = (cz1 + Sz - (cz0 - Sz) + 1) * max(nyr, 0);
-    for (int rr = part; rr < nrows; rr += kRealSplit) {
+    for (int rr = part; rr < nrows; rr += SPLIT) {
         const int nzu = cz0 - Sz + rr / nyr, ny = ny_lo + rr % nyr;
         const int wrap = nzu >= 0 ? nzu / g.ncz : -((-nzu + g.ncz - 1) / g.ncz);
         const int nz = nzu - wrap * g.ncz;
@@ -318,7 +323,7 @@ __global__ void __launch_bounds__(32 * kRealWarps) k_real(Geo g, int n, const in
         afz += __shfl_xor_sync(full, afz, o);
     }
     if (valid && half == 0) {
-        // the kRealSplit warps of a target group combine through FP64 atomics
+        // the SPLIT warps of a target group combine through FP64 atomics
         // (outputs are zeroed beforehand when not accumulating)
         const double qm = (accumulate & 2) ? 1.0 : (double)qme;  // bit 1: field instead of force
         atomicAdd(phi + orig, aphi);
@@ -340,9 +345,18 @@ void launch_real_space(se1p_plan *p, int n, const int *cell_key, double *phi, do
         cudaMemsetAsync(phi, 0, sizeof(double) * (size_t)n, s);
         cudaMemsetAsync(frc, 0, sizeof(double) * 3 * (size_t)n, s);
     }
-    const int warps = (n + kRealTargets - 1) / kRealTargets * kRealSplit;
-    k_real<T><<<(warps + kRealWarps - 1) / kRealWarps, 32 * kRealWarps, 0, s>>>(
-        g, n, p->b.starts + g.nbins + 1, (const CellRec<T> *)p->b.cells, cell_key, phi, frc, accumulate);
+    // expected neighbours of a target within rc at uniform density
+    const double neighbours = n / (g.L[0] * g.L[1] * g.L[2]) * 4.0 / 3.0 * kPi * g.rc * g.rc * g.rc;
+    const int groups = (n + kRealTargets - 1) / kRealTargets;
+    if (neighbours >= kRealSplitNeighbours) {
+        const int warps = groups * 4;
+        k_real<T, 4><<<(warps + kRealWarps - 1) / kRealWarps, 32 * kRealWarps, 0, s>>>(
+            g, n, p->b.starts + g.nbins + 1, (const CellRec<T> *)p->b.cells, cell_key, phi, frc, accumulate);
+    } else {
+        const int warps = groups * 2;
+        k_real<T, 2><<<(warps + kRealWarps - 1) / kRealWarps, 32 * kRealWarps, 0, s>>>(
+            g, n, p->b.starts + g.nbins + 1, (const CellRec<T> *)p->b.cells, cell_key, phi, frc, accumulate);
+    }
 }
 
 template void launch_real_space<float>(se1p_plan *, int, const int *, double *, double *, int, cudaStream_t);

@@ -1,0 +1,53 @@
+"""Host-side bookkeeping of bench.py (no GPU): kernel launch counts, per-stage rooflines."""
+import math
+
+import bench
+
+
+C2_INFO = dict(P=24, Mt=96, M3=64, n0=288, nI=192, n_I_modes=4, cells=[20, 20, 20])
+C3_INFO = dict(P=24, Mt=160, M3=1024, n0=480, nI=320, n_I_modes=32, cells=[33, 33, 266])
+PEAKS = {"hbm_gbs": 6794.8, "sm_max_mhz": 2070.0}
+
+
+def test_kernels_per_eval_matches_the_launch_lists():
+    # ncu launch lists: 190 launches for 10 evaluations at N = 10^5 (pack, scan, scatter, spread, z pass,
+    # 3 x 3 slab-class passes, z pass, gather, real space, finalize, energy); at N = 10^6 in [1,1,8]
+    # the 290 037 real-space cells add the three-kernel multi-block scan
+    assert bench.kernels_per_eval(C2_INFO, True) == 19
+    assert bench.kernels_per_eval(C3_INFO, True) == 22
+    assert bench.kernels_per_eval(C2_INFO, False) == 18
+    # no mode in the set I: one slab class less
+    assert bench.kernels_per_eval(dict(C2_INFO, n_I_modes=0), True) == 16
+
+
+def test_stage_rooflines_report_each_stage_against_its_bound():
+    ms = {"pack": 0.8, "spread": 5.0, "fourier": 0.8, "gather": 4.0, "real": 9.0, "final": 0.1}
+    n, P = 100_000, 24
+    pairs = n * 1e5 * 4.0 / 3.0 * math.pi * 0.15 ** 3
+    r = bench.stage_rooflines(ms, 10, C2_INFO, n, "mixed", PEAKS, P, pairs)
+    assert set(r) == set(ms)
+    fp32 = 152 * 128 * 2 * 2070e6 / 1e12
+    for k in ("spread", "gather", "real"):
+        assert r[k]["bound"] == "alu" and r[k]["unit"] == "TFLOP/s"
+        assert r[k]["peak"] == fp32
+    for k in ("pack", "fourier", "final"):
+        assert r[k]["bound"] == "hbm" and r[k]["unit"] == "GB/s" and r[k]["peak"] == PEAKS["hbm_gbs"]
+    for v in r.values():
+        assert v["frac"] == v["achieved"] / v["peak"]
+    # spread: 2 P^3 flop per particle over its time per evaluation
+    assert math.isclose(r["spread"]["achieved"], n * 2 * P ** 3 / 0.5e-3 / 1e12)
+    assert math.isclose(r["real"]["achieved"], pairs * 40 / 0.9e-3 / 1e12)
+    # FP64 runs against the FP64 rate, and its Fourier passes move twice the FP32 grid bytes
+    r64 = bench.stage_rooflines(ms, 10, C2_INFO, n, "fp64", PEAKS, P, pairs)
+    assert r64["spread"]["peak"] == 1.25
+    assert bench.fourier_bytes(C2_INFO, 8) > bench.fourier_bytes(C2_INFO, 4)
+
+
+def test_roofline_picks_the_dominant_stage():
+    ms = {"pack": 0.8, "spread": 5.0, "fourier": 4.0, "gather": 4.0, "real": 14.0, "final": 0.1}
+    info = dict(C2_INFO, density=1e5, rc=0.15)
+    rf = bench.roofline(ms, 10, info, 100_000, "mixed", PEAKS, 2070.0, "c2")
+    assert rf["kernel"] == "k_real" and rf["bound"] == "alu"
+    ms["spread"] = 20.0
+    rf = bench.roofline(ms, 10, info, 100_000, "mixed", PEAKS, 2070.0, "c2")
+    assert rf["kernel"] == "k_spread"

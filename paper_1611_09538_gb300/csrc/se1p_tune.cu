@@ -174,7 +174,8 @@ se1p_status se1p_batch_create(int count, const se1p_params *params, const int *n
         b->n_max.push_back(n_max[i]);
     }
     // worker streams of the captured graph (systems round-robin): independent branches let small
-    // systems run side by side (64 systems of 1k-50k charges: 21.6 ms with 8, 18.1 ms with 32)
+    // systems run side by side (64 systems of 1k-50k charges: 21.6 ms with 8, 18.1 ms with 32,
+    // 18.3 ms with 64)
     const int ns = count < 32 ? count : 32;
     for (int k = 0; k < ns; ++k) {
         cudaStream_t s;

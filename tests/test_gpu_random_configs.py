@@ -191,3 +191,25 @@ def test_random_configurations_in_one_batch(precision):
             if eta < 1.0:
                 assert rel(phi[a:c], phi_ref) < 1e-5, prm
                 assert rel(F[a:c], F_ref) < 1e-5, prm
+
+
+@pytest.mark.parametrize("M3,P", [(4, 4), (5, 5), (6, 4)])
+def test_periodic_axis_shorter_than_a_tile(M3, P):
+    """A periodic axis of fewer grid points than one 8-point gridding tile (M3 < 8, P up to M3): the
+    tile's rows beyond M3 are never written and every window wraps around the whole axis."""
+    L = (1.0, 1.0, 0.25)
+    M = (16, 16, M3)
+    n = 150
+    x, q = inputs.uniform_shifted(n, L, seed=5000 + M3)
+    Mt = smooth_at_least(M[0] + P)
+    prm = dict(L=L, xi=8.0, M=M, P=P, Mt=Mt, n0=smooth_at_least(3 * Mt), nI=smooth_at_least(2 * Mt), nl=1,
+               rc=0.2)
+    phi_ref, F_ref = reference_parts(x, q, prm)
+    for prec in (se1p.SE1P_FP64, se1p.SE1P_MIXED):
+        plan = se1p.Plan(L, prm["xi"], M, P, n, Mt=Mt, n0=prm["n0"], nI=prm["nI"], nl=1, rc=0.2, precision=prec)
+        r = plan.eval(torch.as_tensor(x, device="cuda"), torch.as_tensor(q, device="cuda"))
+        phi, F = r.phi.cpu().numpy(), r.force.cpu().numpy()
+        plan.close()
+        tol = 1e-9 if prec == se1p.SE1P_FP64 else 1e-5
+        assert np.max(np.abs(phi - phi_ref)) < tol * np.max(np.abs(phi_ref)), (M3, P, prec)
+        assert np.max(np.abs(F - F_ref)) < tol * np.max(np.abs(F_ref)), (M3, P, prec)

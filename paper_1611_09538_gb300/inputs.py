@@ -84,7 +84,7 @@ def cloud_wall_like(n: int, L: float, seed: int = 5) -> tuple[np.ndarray, np.nda
     does not give: a strongly polar arrangement with a large dipole along the free axis x.
     Charges +1 (first half): x ~ L/2 + N(0, (0.01 L)^2), y, z uniform.  Charges -1 (second
     half): a Gaussian cloud around (L/4, L/2, L/2) with sigma = L/10.  x, y samples outside
-    [0, L) are redrawn; z is wrapped.  Neutral for even n."""
+    [0, L) are redrawn; z is wrapped.  Neutral (for odd n one wall charge is 0)."""
     rng = np.random.default_rng(seed)
     n_wall = n - n // 2
     x = np.empty((n, 3))
@@ -106,8 +106,8 @@ def cloud_wall_like(n: int, L: float, seed: int = 5) -> tuple[np.ndarray, np.nda
     x[:, 2] = np.mod(x[:, 2], L)
     x[:, 2][x[:, 2] >= L] = 0.0
     q = np.where(np.arange(n) < n_wall, 1.0, -1.0)
-    if n % 2 == 1:
-        q[-1] = 0.0
+    if n % 2 == 1:  # odd n: the wall holds one charge more; keep the system neutral
+        q[n_wall - 1] = 0.0
     return x, q
 
 

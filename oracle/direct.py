@@ -1,4 +1,5 @@
-"""ctypes front end of the FP64 direct Ewald1P oracle (ewald1p_direct.c).
+"""ctypes front end of the FP64 direct Ewald oracles: Ewald1P (ewald1p_direct.c) and, for the
+triply periodic comparison method, Ewald3P (ewald3p_direct.c).
 
 TEST INFRASTRUCTURE ONLY: the tests, the package smoke check and the
 benchmark's CPU-baseline leg are the only callers.  The shared object is built
@@ -15,6 +16,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ewald1p_direct.c")
+_SRC3 = os.path.join(_HERE, "ewald3p_direct.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_OUT_DIR, "libewald1p_oracle.so")
 _lib = None
@@ -24,10 +26,10 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2, OpenMP, no fast-math) if it is stale."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC3))):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, _SRC3, "-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, _LIB)
     return _LIB
@@ -48,6 +50,8 @@ def _load():
         lib.orc_kinc_mdb.argtypes = [d, d]
         lib.orc_ewald1p.restype = i
         lib.orc_ewald1p.argtypes = [i, p, p, i, p, d, d, d, d, p, p]
+        lib.orc_ewald3p.restype = i
+        lib.orc_ewald3p.argtypes = [i, p, p, i, p, p, d, d, d, p, p]
         lib.orc_num_threads.restype = i
         lib.orc_num_threads.argtypes = []
         _lib = lib
@@ -114,6 +118,30 @@ def ewald1p(x, q, L3, xi, rc, targets=None, kcut=1e-20):
     if targets is None:
         U = 0.5 * float(np.dot(np.asarray(q, dtype=np.float64), phi))
     return phi, F, U
+
+
+def ewald3p_parts(x, q, L, xi, rc, targets=None, kcut=1e-20):
+    """Per-target parts of the triply periodic Ewald potential and force (tin-foil boundary).
+
+    Returns (phi_parts [nt,3]: R, F, self; force_parts [nt,2,3]: R, F).  rc <= 0 skips the
+    real space."""
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    Lv = np.ascontiguousarray(L, dtype=np.float64)
+    n = x.shape[0]
+    if targets is None:
+        nt, tptr, tg = n, None, None
+    else:
+        tg = np.ascontiguousarray(targets, dtype=np.int32)
+        nt, tptr = tg.size, tg.ctypes.data
+    phi = np.zeros((nt, 3))
+    frc = np.zeros((nt, 2, 3))
+    rcode = lib.orc_ewald3p(n, x.ctypes.data, q.ctypes.data, nt, tptr, Lv.ctypes.data, float(xi),
+                            float(rc) if rc is not None else -1.0, float(kcut), phi.ctypes.data, frc.ctypes.data)
+    if rcode != 0:
+        raise ValueError("oracle rejected its arguments")
+    return phi, frc
 
 
 if __name__ == "__main__":  # pragma: no cover

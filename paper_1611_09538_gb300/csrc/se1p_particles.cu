@@ -257,31 +257,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_write(int len, const int 
     }
 }
 
-// e^x in FP32 for the window exponents, x in [-87, 0]: e^x = 2^n e^r with
-// n = rint(x / ln 2) and r = x - n ln 2 (Cody and Waite's reduction: ln 2 in two
-// parts, the first with 8 trailing zero bits so that n * hi is exact for |n| < 256),
-// e^r by its Taylor series to r^8 (|r| <= ln 2 / 2, truncation < 3e-10), 2^n exact.
-// Every step rounds to nearest, so the result (within ~1.2 ulp) has no systematic
-// bias, which a window value must not have: the FP32 grid's self-interaction of
-// each charge would carry it into the energy.
-__device__ __forceinline__ float exp_window(float x)
-{
-    x = fmaxf(x, -87.0f);  // keeps 2^n normal; e^-87 ~ 1.6e-38 is below any window value used
-    const float n = rintf(x * 1.44269504088896341f);
-    float r = fmaf(n, -0.693145751953125f, x);
-    r = fmaf(n, -1.42860677e-06f, r);
-    float p = 2.48015873e-05f;  // 1/8!
-    p = fmaf(p, r, 1.98412698e-04f);
-    p = fmaf(p, r, 1.38888889e-03f);
-    p = fmaf(p, r, 8.33333333e-03f);
-    p = fmaf(p, r, 4.16666667e-02f);
-    p = fmaf(p, r, 1.66666667e-01f);
-    p = fmaf(p, r, 0.5f);
-    p = fmaf(p, r, 1.0f);
-    p = fmaf(p, r, 1.0f);
-    return p * __int_as_float(((int)n + 127) << 23);
-}
-
 // Scatter into bin order (with the window tables) and into cell order.  One thread per
 // particle computes its window values into a per-warp shared buffer (row stride 3P + 1, so the
 // lanes' rows start in different banks); the warp then writes each particle's row of 3P values

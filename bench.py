@@ -33,8 +33,8 @@ if ROOT not in sys.path:
 METRIC = "particles/sec (phi+force) at rms rel err 1e-6, mixed vs FP64 GPU; % HBM roofline"
 UNIT = "particles/s"
 L2_BYTES = 129 * 1024 * 1024
-FP32_LANES_PER_SM = 128
-NUM_SMS = 152
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (Blackwell SM: 4 partitions x 32)
+FP64_FMA_PER_SM_CLK = 2   # FP64 FMA per SM per clock on GB300 (1.25 TFLOP/s nominal at 152 SMs, 2.07 GHz)
 
 
 def parse():
@@ -44,7 +44,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="se1p", choices=["se1p", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c3p", "c4"],
+                    help="c3: the elongated box on the grid that resolves xi = 40; c3p: the same charges on the "
+                         "printed grid 64x64x512 (outside the 1e-6 bar, reading A17); c4: the clustered box")
+    ap.add_argument("--vjp", action="store_true",
+                    help="also time the adjoint se1p_eval_vjp (the potential's vector-Jacobian product)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-extras", action="store_true",
@@ -53,6 +57,9 @@ def parse():
                     help="FFT-stage runtime ratio, plain upsampled FFT / AFT (Table 5.1), then exit")
     ap.add_argument("--table-6-2", action="store_true",
                     help="whole-evaluation throughput on the shapes of Table 6.2 (cloud-wall stand-in), then exit")
+    ap.add_argument("--table-6-1-ratio", action="store_true",
+                    help="k-space runtime of SE1P over the triply periodic SE3P on the systems of Table 6.1 "
+                         "(Example 6.5), then exit")
     ap.add_argument("--profile-only", action="store_true",
                     help="only warm-up + timed steps (for ncu launch lists); prints a short line")
     return ap.parse_args()
@@ -62,13 +69,15 @@ def workload(name):
     from paper_1611_09538_gb300 import inputs
     # c3: the elongated box on the grid that resolves xi = 40 (on the printed grid, eta = 3.3 > 1,
     # the mixed path cannot reach rms 1e-6, so no throughput at that accuracy exists there)
-    return {"c1": inputs.config_c1, "c2": inputs.config_c2, "c3": inputs.config_c3_resolved}[name]()
+    return {"c1": inputs.config_c1, "c2": inputs.config_c2, "c3": inputs.config_c3_resolved,
+            "c3p": inputs.config_c3, "c4": inputs.config_c4}[name]()
 
 
 def workload_config(sys_, name, precision):
     p = sys_.params
     return {
-        "workload": f"{sys_.name or name.upper()}: N={len(sys_.q)} uniform charges, L={list(sys_.L)}, xi={p['xi']}, "
+        "workload": f"{sys_.name or name.upper()}: N={len(sys_.q)} {'clustered' if name == 'c4' else 'uniform'} "
+                    f"charges, L={list(sys_.L)}, xi={p['xi']}, "
                     f"M={list(p['M'])}, P={p['P']}, Mt={p['Mt']}, n0={p['n0']}, nI={p['nI']}, nl={p['nl']}, "
                     f"rc={p['rc']}",
         "N": len(sys_.q), "precision": precision, "L2": "flushed between timed steps (256 MiB write)",
@@ -193,46 +202,73 @@ def committed_traffic(kernel, workload_name):
     return ent.get("dram_bytes_per_launch")
 
 
-def roofline(stage_ms, n_evals, info, n, precision, peaks, clock_mhz, workload_name):
+def count_pairs(x, L, rc):
+    """Exact number of ordered target-source pairs (z images included, the target itself
+    excluded) with 0 < r <= rc: the pair terms the real-space kernel evaluates (Eq. 2.2).
+    Host k-d tree over the sources and their z images within rc."""
+    from scipy.spatial import cKDTree
+    x = np.asarray(x, dtype=np.float64)
+    k = int(math.ceil(rc / L[2]))
+    imgs = np.concatenate([x + np.array([0.0, 0.0, j * L[2]]) for j in range(-k, k + 1)])
+    return int(cKDTree(x).count_neighbors(cKDTree(imgs), rc)) - len(x)
+
+
+def alu_peaks(se1p, mhz):
+    """FP32 and FP64 FMA peaks in TFLOP/s: derived from the unit counts (multiprocessor count read
+    from the device x FMA lanes x 2 flop x maximum SM clock) and measured by the library's FMA-loop
+    microbenchmark under the clocks of this run."""
+    f32, sms = se1p.se1p_measure_fma_peak(se1p.SE1P_MIXED)
+    f64, _ = se1p.se1p_measure_fma_peak(se1p.SE1P_FP64)
+    return {"sms": sms, "sm_max_mhz": mhz,
+            "fp32_derived": sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, "fp32_measured": f32,
+            "fp64_derived": sms * FP64_FMA_PER_SM_CLK * 2 * mhz * 1e6 / 1e12, "fp64_measured": f64}
+
+
+def alu_peak_for(alu, precision):
+    """The roofline denominator of an arithmetic-bound kernel: the unit-count peak, and its source."""
+    key = "fp32" if precision == "mixed" else "fp64"
+    return alu[f"{key}_derived"], (f"derived: {alu['sms']} SMs x "
+                                   f"{FP32_LANES_PER_SM if key == 'fp32' else FP64_FMA_PER_SM_CLK} {key.upper()} "
+                                   f"FMA/clk x 2 flop x {alu['sm_max_mhz']:.0f} MHz; FMA-loop measured "
+                                   f"{alu[key + '_measured']:.2f} TFLOP/s")
+
+
+def roofline(stage_ms, n_evals, info, n, precision, peaks, alu, pairs, workload_name):
     """Roofline of the dominant stage (largest share of the step)."""
     P = info["P"]
     per = {k: v / max(n_evals, 1) for k, v in stage_ms.items()}
     dom = max(per, key=per.get)
-    lanes = NUM_SMS * FP32_LANES_PER_SM
-    mhz = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = lanes * 2 * mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
-    # FP64 (non-tensor) rate of this part: 1.25 TFLOP/s nominal (64x below FP32)
-    fp64_peak = 1.25
-    peak_alu = fp32_peak if precision == "mixed" else fp64_peak
+    peak_alu, alu_src = alu_peak_for(alu, precision)
     t = per[dom] * 1e-3
     word = 4 if precision == "mixed" else 8
     grid_pts = info["M3"] * info["Mt"] * info["Mt"]
     if dom == "gather":
-        flops = n * 4.0 * P ** 3  # two FMA per support point: phi and the x-derivative chain
+        flops = n * 4.0 * P ** 3  # 2 P^3 FMA: phi and the x-derivative chain (y, z chains reuse them)
         return dict(kernel="k_gather", bound="alu", achieved=flops / t / 1e12, peak=peak_alu, unit="TFLOP/s",
                     frac=flops / t / 1e12 / peak_alu, traffic=committed_traffic("k_gather", workload_name),
-                    algorithmic=f"{4 * P ** 3} flop/particle", stage_ms=per)
+                    algorithmic=f"{4 * P ** 3} flop/particle", stage_ms=per, peak_source=alu_src)
     if dom == "spread":
         flops = n * 2.0 * P ** 3  # one FMA per support point
         return dict(kernel="k_spread", bound="alu", achieved=flops / t / 1e12, peak=peak_alu, unit="TFLOP/s",
                     frac=flops / t / 1e12 / peak_alu, traffic=committed_traffic("k_spread", workload_name),
-                    algorithmic=f"{2 * P ** 3} flop/particle", stage_ms=per)
+                    algorithmic=f"{2 * P ** 3} flop/particle", stage_ms=per, peak_source=alu_src)
     if dom == "fourier":
         # read + write of the real grid twice (z passes) and of every slab row in the 2-D passes
         byts = grid_pts * word * 4
         return dict(kernel="fourier passes", bound="hbm", achieved=byts / t / 1e9, peak=peaks["hbm_gbs"],
                     unit="GB/s", frac=byts / t / 1e9 / peaks["hbm_gbs"], traffic=None,
-                    algorithmic=f"{byts} B/step", stage_ms=per)
+                    algorithmic=f"{byts} B/step", stage_ms=per, peak_source="measured hbm_gbs")
     if dom == "real":
-        # erfc/exp pair evaluations inside rc: ~ N * rho * 4/3 pi rc^3 pairs, ~40 flops each
-        pairs = n * info["density"] * 4.0 / 3.0 * math.pi * info["rc"] ** 3
+        # erfc/exp pair evaluations inside rc (exact count on the host), 40 flop each
         flops = pairs * 40.0
         return dict(kernel="k_real", bound="alu", achieved=flops / t / 1e12, peak=peak_alu, unit="TFLOP/s",
                     frac=flops / t / 1e12 / peak_alu, traffic=committed_traffic("k_real", workload_name),
-                    algorithmic="40 flop/pair inside rc", stage_ms=per)
+                    algorithmic=f"40 flop/pair inside rc x {pairs} pairs (exact host count)", stage_ms=per,
+                    peak_source=alu_src)
     byts = n * 64.0
     return dict(kernel=dom, bound="hbm", achieved=byts / t / 1e9, peak=peaks["hbm_gbs"], unit="GB/s",
-                frac=byts / t / 1e9 / peaks["hbm_gbs"], traffic=None, algorithmic="64 B/particle", stage_ms=per)
+                frac=byts / t / 1e9 / peaks["hbm_gbs"], traffic=None, algorithmic="64 B/particle", stage_ms=per,
+                peak_source="measured hbm_gbs")
 
 
 def fourier_bytes(info, word):
@@ -251,12 +287,11 @@ def fourier_bytes(info, word):
     return b
 
 
-def stage_rooflines(stage_ms, n_evals, info, n, precision, peaks, P, pairs):
+def stage_rooflines(stage_ms, n_evals, info, n, precision, peaks, P, pairs, alu_peak):
     """Each stage of the evaluation against its own bound, from times taken with the stages run in
     sequence (profiling mode 2): spread and gather against the FP32 (FP64) FMA peak, the real space
     at 40 flop per pair, the Fourier passes and the particle bookkeeping against HBM."""
-    mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu = NUM_SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12 if precision == "mixed" else 1.25
+    alu = alu_peak
     hbm = peaks["hbm_gbs"]
     word = 4 if precision == "mixed" else 8
     rec = 32 if precision == "mixed" else 48
@@ -382,6 +417,8 @@ def run_gpu(args, rank, world, local_rank):
         Fm = r.force.cpu().numpy()
         ref.close()
 
+    peaks, peak_src = read_peaks()
+    alu = alu_peaks(se1p, peaks.get("sm_max_mhz", 2070.0))
     sampler = ClockSampler(local_rank)
     time.sleep(0.25)
     se1p.se1p_plan_set_profiling(plan.handle, True)
@@ -435,12 +472,12 @@ def run_gpu(args, rank, world, local_rank):
             dist.destroy_process_group()
         return
 
-    peaks, peak_src = read_peaks()
     ms_per_step = total_ms / args.steps
     value = job_rate(n * args.steps, world, total_ms * 1e-3)
-    rf = roofline(stage_ms, n_evals, info, n, args.precision, peaks, clocks and clocks["sm_mhz"], args.workload)
-    rf["peak_source"] = ("derived: 152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz" if rf["bound"] == "alu"
-                         else f"{peak_src} hbm_gbs")
+    pairs = count_pairs(sys_.x, sys_.L, p["rc"]) if p["rc"] > 0 else 0
+    rf = roofline(stage_ms, n_evals, info, n, args.precision, peaks, alu, pairs, args.workload)
+    if rf["bound"] == "hbm":
+        rf["peak_source"] = f"{peak_src} hbm_gbs"
     launches_per_eval = kernels_per_eval(info, p["rc"] > 0)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -457,12 +494,15 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": int(launches_per_eval * args.steps),
         "clocks": clocks,
         "accuracy": acc,
-        "stages_alone": stage_rooflines(alone_ms, alone_n, info, n, args.precision, peaks, p["P"],
-                                        n * info["density"] * 4.0 / 3.0 * math.pi * p["rc"] ** 3),
+        "stages_alone": stage_rooflines(alone_ms, alone_n, info, n, args.precision, peaks, p["P"], pairs,
+                                        alu_peak_for(alu, args.precision)[0]),
+        "alu_peaks": alu, "real_space_pairs": pairs,
     }
     if not args.no_extras:
         out["fp64"] = measure_fp64(sys_, p, n, x, q, stream, min(args.steps, 20))
         out["batched"] = measure_batched(stream)
+    if args.vjp:
+        out["vjp"] = measure_vjp(plan, n, x, q, stream, min(args.steps, 20), args.precision)
     if not args.no_cpu_baseline and world == 1:
         cb = oracle_sample(sys_, args.cpu_seconds)
         t = cb["targets"]
@@ -499,6 +539,31 @@ def measure_fp64(sys_, p, n, x, q, stream, steps):
     ms = a.elapsed_time(b) / steps
     plan.close()
     return {"value": n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps}
+
+
+def measure_vjp(plan, n, x, q, stream, steps, precision):
+    """Throughput of the adjoint of phi (se1p_eval_vjp: two field evaluations with the grid recomputed,
+    then the combine), inputs resident, a fixed random cotangent.  The energy's gradient needs no
+    adjoint: dU/dx = -F and dU/dq = phi come with every se1p_eval."""
+    import torch
+    from paper_1611_09538_gb300 import se1p
+    g = torch.Generator(device="cuda").manual_seed(9)
+    v = torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
+    gx = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    gq = torch.empty(n, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        se1p.se1p_eval_vjp(plan.handle, n, x, q, v, gx, gq, stream)
+    st = se1p.se1p_plan_sync_status(plan.handle, stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(steps):
+        se1p.se1p_eval_vjp(plan.handle, n, x, q, v, gx, gq, stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    return {"value": n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "precision": precision,
+            "status": se1p.STATUS.get(st), "what": "se1p_eval_vjp: dl/dx and dl/dq for a cotangent of phi"}
 
 
 def measure_batched(stream, steps=5):
@@ -642,6 +707,61 @@ def table_6_2(args):
         plan.close()
 
 
+def table_6_1_ratio(args):
+    """Example 6.5: the k-space part (pack, gridding, Fourier stage, gathering; no real space) of
+    SE1P and of the triply periodic SE3P on the uniform systems of Table 6.1 (N/L^3 = 125, xi = 4,
+    charges U[-1,1] minus their mean), with the printed M and n_l and P = 12, s_l = 2 for 1e-5 and
+    P = 24, s_l = 3 for 1e-9; both methods use the same M and P (the printed M rounded up to the next
+    2^a 3^b 5^c 7^d size, since SE3P transforms the M grid itself).  Stage times come from profiling
+    mode 2 (stages one after another), CUDA events, inputs resident.  One JSON line per row."""
+    import torch
+    from paper_1611_09538_gb300 import build as lib_build
+    from paper_1611_09538_gb300 import inputs, se1p
+    lib_build.build()
+    prec = se1p.SE1P_MIXED if args.precision == "mixed" else se1p.SE1P_FP64
+    with open(os.path.join(ROOT, "tests", "golden", "table_6_1.json")) as f:
+        tab = json.load(f)["table_6_1"]
+    steps = max(args.steps, 10)
+
+    def kspace_ms(plan, x, q):
+        for _ in range(max(args.warmup, 3)):
+            plan.eval(x, q, check=False)
+        se1p.se1p_plan_set_profiling(plan.handle, 2)
+        for _ in range(steps):
+            plan.eval(x, q, check=False)
+        ms, ne = se1p.se1p_plan_stage_times(plan.handle)
+        st = se1p.se1p_plan_sync_status(plan.handle)
+        per = {k: v / ne for k, v in ms.items()}
+        return per, se1p.STATUS.get(st)
+
+    for tol, P, sl, mcol, ncol in (("1e-5", 12, 2.0, 2, 3), ("1e-9", 24, 3.0, 4, 5)):
+        for row in tab["rows"]:
+            # the SE3P FFTs run on M itself: the printed M rounded up to a 2^a 3^b 5^c 7^d size, for both
+            N, Lb, M, nl = int(row[0]), float(row[1]), smooth_at_least(int(row[mcol])), int(row[ncol])
+            L = (Lb, Lb, Lb)
+            xn, qn = inputs.uniform_shifted(N, L, seed=61)
+            x = torch.as_tensor(xn, device="cuda")
+            q = torch.as_tensor(qn, device="cuda")
+            p1 = se1p.Plan(L, tab["xi"], (M, M, M), P, N, nl=nl, sl=sl, rc=0.0, precision=prec)
+            t1, s1 = kspace_ms(p1, x, q)
+            i1 = p1.info
+            p1.close()
+            p3 = se1p.Plan(L, tab["xi"], (M, M, M), P, N, rc=0.0, precision=prec,
+                           flags=se1p.SE1P_FLAG_TRIPLY_PERIODIC)
+            t3, s3 = kspace_ms(p3, x, q)
+            p3.close()
+            k1 = sum(t1[k] for k in ("pack", "spread", "fourier", "gather"))
+            k3 = sum(t3[k] for k in ("pack", "spread", "fourier", "gather"))
+            print(json.dumps({"table": "6.1", "example": "6.5", "tol": tol, "N": N, "L": Lb, "M": M,
+                              "M_printed": int(row[mcol]), "nl": nl,
+                              "P": P, "sl": sl, "precision": args.precision, "Mt": i1["Mt"], "n0": i1["n0"],
+                              "nI": i1["nI"], "status": [s1, s3],
+                              "kspace_ms_se1p": k1, "kspace_ms_se3p": k3, "ratio_kspace": k1 / k3,
+                              "fourier_ms_se1p": t1["fourier"], "fourier_ms_se3p": t3["fourier"],
+                              "ratio_fourier": t1["fourier"] / t3["fourier"],
+                              "stages_se1p": t1, "stages_se3p": t3}), flush=True)
+
+
 # ------------------------------------------------------------------ reference arm (the oracle)
 def oracle_step(sys_, n_sources, seed):
     """One reference step: the direct sums for one target against n_sources of the N sources.
@@ -703,6 +823,8 @@ def main():
         aft_table(args)
     elif args.table_6_2:
         table_6_2(args)
+    elif args.table_6_1_ratio:
+        table_6_1_ratio(args)
     else:
         run_gpu(args, rank, world, local_rank)
 

@@ -79,8 +79,23 @@ typedef struct {
     double rc;     /* real-space cutoff; <= 0 skips phi^R (k-space and self only)      */
     double tol;    /* tolerance for the automatic choices (<= 0: 1e-10)                */
     int precision; /* se1p_precision                                                    */
-    int flags;     /* reserved, must be 0                                               */
+    int flags;     /* 0, or SE1P_FLAG_TRIPLY_PERIODIC                                  */
 } se1p_params;
+
+/*
+ * SE1P_FLAG_TRIPLY_PERIODIC selects the triply periodic Spectral Ewald method
+ * (SE3P), the method the paper measures SE1P against (Section 1, Example 6.5):
+ * x and y are periodic as well, with periods L[0] = L[1], and the Green's
+ * function is 1/k^2 for every k != 0 with no k = 0 term (a neutral system in a
+ * conducting medium).  No axis is padded: the FFTs run on the M[0] x M[1] x M[2]
+ * periodic grid (M[0] a 2^a 3^b 5^c 7^d size); Mt, n0, nI, nl, s0, sl are
+ * ignored.  Gridding and gathering run on the same M + P extended grid as SE1P
+ * and the P-wide overhang is folded onto the periodic grid (and unfolded before
+ * gathering).  Requires an even P and rc <= min(L).  x and y are wrapped into
+ * [0, L) like z.  The single-step entry points se1p_spread, se1p_fourier and
+ * se1p_gather are not available for such plans (SE1P_ERR_INVALID_ARG).
+ */
+#define SE1P_FLAG_TRIPLY_PERIODIC 1
 
 /* Resolved plan geometry (read-only view). */
 typedef struct {
@@ -100,7 +115,10 @@ typedef struct se1p_plan se1p_plan;
  * Validates params (SE1P_ERR_INVALID_ARG), resolves the automatic fields,
  * allocates the workspace (SE1P_ERR_ALLOC) and precomputes, in FP64 on the
  * device, the k3 = 0 scaling table 4 pi e^{-(1-eta) kappa^2/4 xi^2} G_R(kappa)
- * (Eqs. 3.9-3.10).  Synchronous.  *plan is NULL on failure. */
+ * (Eqs. 3.9-3.10).  Synchronous.  *plan is NULL on failure; a failed allocation
+ * frees everything the call allocated before it.  For tests of that path, the
+ * environment variable SE1P_TEST_FAIL_ALLOC=k (k >= 1) makes the k-th workspace
+ * allocation of every plan creation fail (SE1P_ERR_ALLOC) without asking CUDA. */
 se1p_status se1p_plan_create(const se1p_params *params, int n_max, se1p_plan **plan);
 
 /* Free a plan and its workspace (synchronises the device first).  NULL is a no-op. */
@@ -156,8 +174,9 @@ se1p_status se1p_fourier(se1p_plan *plan, const double *grid_in, double *grid_ou
 se1p_status se1p_gather(se1p_plan *plan, int n, const double *x, const double *q,
                         const double *grid, double *phi, double *force, void *stream);
 
-/* Real-space part, Eq. 2.2 and its force (Eq. 3.22), over a cell list with cells
- * no smaller than rc.  Writes (does not accumulate) phi and force.  Requires
+/* Real-space part, Eq. 2.2 and its force (Eq. 3.22), over a cell list whose cells
+ * have an edge of at least rc/3 (a target's sources lie within ceil(rc / edge)
+ * cells per axis).  Writes (does not accumulate) phi and force.  Requires
  * params.rc > 0 and rc <= L3. */
 se1p_status se1p_real_space(se1p_plan *plan, int n, const double *x, const double *q, double *phi,
                             double *force, void *stream);
@@ -222,7 +241,7 @@ se1p_status se1p_autotune(const se1p_tune_request *req, se1p_params *out);
  * evaluates all systems from packed arrays: system i occupies particles
  * offsets[i] .. offsets[i+1]-1 (host array of count+1 ints) of x [*][3], q, phi,
  * force; energy[i] receives its U.  The work of all systems is captured once
- * into a CUDA graph (nodes spread over up to 8 streams, so small systems run
+ * into a CUDA graph (nodes spread over up to 32 streams, so small systems run
  * concurrently) and replayed with one graph launch per call; the graph is
  * re-captured when the sizes or the pointers change.  Device pointers;
  * asynchronous on `stream`.  se1p_batch_sync_status synchronises and returns
@@ -255,14 +274,28 @@ se1p_plan *se1p_batch_plan(se1p_batch *batch, int i);
  *   - x, q, phi, force are device pointers; phi and force must be non-NULL.
  *     Writes (does not accumulate) phi and force.  Inputs are sanitised as in
  *     se1p_eval, but this entry point records no device status.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - Every call made outside stream capture looks up the array's device
+ *     address (cudaGetSymbolAddress) with the current device, so an address
+ *     that a device reset made stale is never used.  A call made while `stream`
+ *     is being captured uses the address found by the last uncaptured call on
+ *     that device: make one call before any stream capture.
  *   - Every call shares the array and leaves its contents behind; calls whose
  *     work overlaps on the GPU race on it and must be serialised by the caller.
  * Asynchronous on `stream`. */
 se1p_status se1p_real_space_noalloc(const se1p_params *params, int n, const double *x, const double *q,
                                     double *phi, double *force, void *stream);
+
+/* ---- device arithmetic peaks (measurement) ----
+ *
+ * se1p_measure_fma_peak: FMA throughput of the current device in TFLOP/s
+ * (2 flop per FMA), FP32 for SE1P_MIXED and FP64 for SE1P_FP64, from a
+ * kernel of independent FMA chains on every SM (best of three ~10 ms launches
+ * after a warm-up).  The gridding, gathering and real-space steps are bound by
+ * this arithmetic rather than by HBM, so their roofline fractions are quoted
+ * against it.  The paper has no counterpart: it times one CPU core.
+ * *sm_count (may be NULL) receives the device's multiprocessor count.
+ * Synchronous; uses the legacy default stream; allocates nothing. */
+se1p_status se1p_measure_fma_peak(int precision, double *tflops, int *sm_count);
 
 /* Static, human-readable name of a status code. */
 const char *se1p_status_string(se1p_status status);

@@ -3,6 +3,7 @@
 // space and self terms, and the single-step entry points.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
@@ -69,12 +70,26 @@ int pow2_fit(size_t per_unit, int cap)
     return v;
 }
 
+// Workspace allocator of plan creation.  Every allocation is recorded in the plan, so a failure
+// part-way frees everything allocated before it.  For tests of that path, the environment variable
+// SE1P_TEST_FAIL_ALLOC = k (k >= 1) makes the k-th allocation of each plan creation fail as if the
+// device or host were out of memory (nothing is requested from CUDA for it).
 struct Alloc {
     se1p_plan *p;
     bool ok = true;
+    int count = 0, fail_at = 0;
+    bool injected()
+    {
+        if (++count == fail_at) {
+            ok = false;
+            return true;
+        }
+        return false;
+    }
     void *dev(size_t bytes)
     {
         if (!ok || bytes == 0) return nullptr;
+        if (injected()) return nullptr;
         void *ptr = nullptr;
         if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
             ok = false;
@@ -88,6 +103,7 @@ struct Alloc {
     void *pinned(size_t bytes)  // page-locked host memory
     {
         if (!ok || bytes == 0) return nullptr;
+        if (injected()) return nullptr;
         void *ptr = nullptr;
         if (cudaMallocHost(&ptr, bytes) != cudaSuccess) {
             ok = false;
@@ -149,7 +165,7 @@ template <typename T> se1p_status build_tables(se1p_plan *p, Alloc &A)
         SlabClass &C = p->cls[c];
         if (C.count == 0) continue;
         C.tw = A.dev((c == 0 ? sizeof(Tw<double>) : sizeof(Tw<T>)) * C.ns);
-        C.rows = A.dev((c == 0 ? csize<double>() : csize<T>()) * (size_t)C.count * p->Mt * C.ns);
+        C.rows = A.dev((c == 0 ? csize<double>() : csize<T>()) * (size_t)C.count * p->Mf * C.ns);
         if (c > 0) C.sym = A.dev(sizeof(T) * (size_t)C.count * C.ns * C.ns);
     }
     if (!A.ok) return SE1P_ERR_ALLOC;
@@ -168,9 +184,10 @@ template <typename T> se1p_status alloc_particles(se1p_plan *p, Alloc &A)
     const int nm = p->n_max > 0 ? p->n_max : 1;
     const Geo &g = p->geo;
     p->b.grid = A.dev(sizeof(T) * (size_t)p->M3 * p->Mt * p->Mt);
-    p->b.zspec = A.dev(csize<T>() * (size_t)p->K3 * p->Mt * p->Mt);
-    p->b.slab0_in = (double *)A.dev(sizeof(double) * (size_t)p->Mt * p->Mt);
-    p->b.slab0_out = (double *)A.dev(sizeof(double) * (size_t)p->Mt * p->Mt);
+    p->b.gridf = p->per3 ? A.dev(sizeof(T) * (size_t)p->M3 * p->Mf * p->Mf) : p->b.grid;
+    p->b.zspec = A.dev(csize<T>() * (size_t)p->K3 * p->Mf * p->Mf);
+    p->b.slab0_in = (double *)A.dev(sizeof(double) * (size_t)p->Mf * p->Mf);
+    p->b.slab0_out = (double *)A.dev(sizeof(double) * (size_t)p->Mf * p->Mf);
     p->b.sym0 = (double *)A.dev(sizeof(double) * (size_t)p->n0 * p->n0);
     p->b.dgrid = (double *)A.dev(sizeof(double) * (size_t)p->M3 * p->Mt * p->Mt);
     p->b.xyzq = (double *)A.dev(sizeof(double) * 4 * (size_t)nm);
@@ -257,7 +274,9 @@ void run_pass(se1p_plan *p, int n, const double *x, const double *q, double *phi
     launch_spread<T>(p, s);
     if (m) m->end(SE1P_STAGE_SPREAD, s);
     if (m) m->begin(SE1P_STAGE_FOURIER, s);
+    if (p->per3) launch_fold<T>(p, s);
     launch_fourier<T>(p, s);
+    if (p->per3) launch_unfold<T>(p, s);
     if (m) m->end(SE1P_STAGE_FOURIER, s);
     if (m) m->begin(SE1P_STAGE_GATHER, s);
     launch_gather<T>(p, n, p->b.grid, phi, frc, 1 | fl | 4, s);
@@ -354,7 +373,9 @@ se1p_status se1p_plan_create(const se1p_params *prm, int n_max, se1p_plan **out)
     if (!(P.xi > 0.0) || !isfinite(P.xi)) return SE1P_ERR_INVALID_ARG;
     if (P.P < 2 || P.P > 32 || P.P > P.M[2] || P.P > P.M[0]) return SE1P_ERR_INVALID_ARG;
     if (P.precision != SE1P_FP64 && P.precision != SE1P_MIXED) return SE1P_ERR_INVALID_ARG;
-    if (P.flags != 0) return SE1P_ERR_INVALID_ARG;
+    if (P.flags != 0 && P.flags != SE1P_FLAG_TRIPLY_PERIODIC) return SE1P_ERR_INVALID_ARG;
+    const bool per3 = P.flags == SE1P_FLAG_TRIPLY_PERIODIC;
+    if (per3 && ((P.P & 1) || !is_smooth(P.M[0]) || (P.rc > 0.0 && P.rc > P.L[0]))) return SE1P_ERR_INVALID_ARG;
     if (!is_smooth(P.M[2])) return SE1P_ERR_INVALID_ARG;
     if (P.rc > 0.0 && (!isfinite(P.rc) || P.rc > P.L[2])) return SE1P_ERR_INVALID_ARG;
     if (P.Mt < 0 || P.n0 < 0 || P.nI < 0) return SE1P_ERR_INVALID_ARG;
@@ -368,18 +389,27 @@ se1p_status se1p_plan_create(const se1p_params *prm, int n_max, se1p_plan **out)
 
     const double tol = P.tol > 0.0 ? P.tol : 1e-10;
     p->M3 = P.M[2];
-    p->Mt = P.Mt > 0 ? P.Mt : next_smooth(P.M[0] + P.P);
-    if (p->Mt < P.M[0] + P.P || !is_smooth(p->Mt)) { delete p; return SE1P_ERR_INVALID_ARG; }
+    p->per3 = per3;
+    if (per3) {
+        // gridding on the extended grid M + P (a multiple of 4, so that gathering can use 16-byte
+        // row vectors), transforms on the periodic grid M: no padding anywhere
+        p->Mt = (P.M[0] + P.P + 3) / 4 * 4;
+        p->Mf = P.M[0];
+    } else {
+        p->Mt = P.Mt > 0 ? P.Mt : next_smooth(P.M[0] + P.P);
+        if (p->Mt < P.M[0] + P.P || !is_smooth(p->Mt)) { delete p; return SE1P_ERR_INVALID_ARG; }
+        p->Mf = p->Mt;
+    }
     const double s0 = P.s0 > 0.0 ? P.s0 : 2.0 * sqrt(2.0);
-    p->n0 = P.n0 > 0 ? P.n0 : next_smooth((long)ceil(s0 * p->Mt - 1e-9));
+    p->n0 = per3 ? p->Mf : (P.n0 > 0 ? P.n0 : next_smooth((long)ceil(s0 * p->Mt - 1e-9)));
     double sl = P.sl;
     if (!(sl > 0.0)) {  // e^{-2 pi sl} < tol (Eq. 4.8)
         sl = -log(tol) / (2.0 * kPi);
         if (sl < 1.0) sl = 1.0;
     }
-    p->nI = P.nI > 0 ? P.nI : next_smooth((long)ceil(sl * p->Mt - 1e-9));
-    p->nl = P.nl >= 0 ? P.nl : (P.M[2] / 10 > 1 ? (int)lround(P.M[2] / 10.0) : 1);  // M ~ 10 nl (Eq. 4.9)
-    if (p->n0 < p->Mt || p->nI < p->Mt || !is_smooth(p->n0) || !is_smooth(p->nI)) { delete p; return SE1P_ERR_INVALID_ARG; }
+    p->nI = per3 ? p->Mf : (P.nI > 0 ? P.nI : next_smooth((long)ceil(sl * p->Mt - 1e-9)));
+    p->nl = per3 ? 0 : (P.nl >= 0 ? P.nl : (P.M[2] / 10 > 1 ? (int)lround(P.M[2] / 10.0) : 1));  // M ~ 10 nl (Eq. 4.9)
+    if (p->n0 < p->Mf || p->nI < p->Mf || !is_smooth(p->n0) || !is_smooth(p->nI)) { delete p; return SE1P_ERR_INVALID_ARG; }
     p->K3 = p->M3 / 2 + 1;
 
     Geo &g = p->geo;
@@ -405,6 +435,7 @@ se1p_status se1p_plan_create(const se1p_params *prm, int n_max, se1p_plan **out)
     g.wnorm_z = sqrt(2.0 * P.xi * P.xi / (kPi * g.etaz));
     g.alpha_xy = 2.0 * P.xi * P.xi * g.h * g.h / g.eta;
     g.alpha_z = 2.0 * P.xi * P.xi * g.hz * g.hz / g.etaz;
+    g.per3 = per3 ? 1 : 0;
     g.rc = P.rc > 0.0 ? P.rc : 0.0;
     g.rc2 = g.rc * g.rc;
     if (g.rc > 0.0) {
@@ -425,14 +456,14 @@ se1p_status se1p_plan_create(const se1p_params *prm, int n_max, se1p_plan **out)
     g.cs[1] = P.L[1] / g.ncy;
     g.cs[2] = P.L[2] / g.ncz;
     int nIm = 0;
-    for (int k = 1; k < p->K3; ++k)
+    for (int k = 1; k < p->K3 && !per3; ++k)
         if (k * P.L[0] / P.L[2] <= p->nl * (1.0 + 1e-12)) nIm = k;
     g.nIm = nIm;
 
     // slab classes: k3 = 0 (FP64), I (nI), J (Mt)
     p->cls[0].ns = p->n0; p->cls[0].kfirst = 0; p->cls[0].count = 1;
     p->cls[1].ns = p->nI; p->cls[1].kfirst = 1; p->cls[1].count = nIm;
-    p->cls[2].ns = p->Mt; p->cls[2].kfirst = 1 + nIm; p->cls[2].count = p->K3 - 1 - nIm;
+    p->cls[2].ns = p->Mf; p->cls[2].kfirst = 1 + nIm; p->cls[2].count = p->K3 - 1 - nIm;
     bool fft_ok = make_fft(p->M3, p->fd_z);
     for (int c = 0; c < 3; ++c) fft_ok = fft_ok && make_fft(p->cls[c].ns, p->cls[c].fd);
     if (!fft_ok) { delete p; return SE1P_ERR_INVALID_ARG; }
@@ -448,12 +479,12 @@ se1p_status se1p_plan_create(const se1p_params *prm, int n_max, se1p_plan **out)
     };
     // z passes: a CTA holds xb_z complex pencils of M3 points (twice, for the Stockham passes); with Mt
     // even each complex pencil carries two real ones
-    p->zpair = p->Mt % 2 == 0;
-    p->xb_z = shrink(pow2_fit(2 * (size_t)p->M3 * cT, 32), (long)p->Mt * p->Mt / (p->zpair ? 2 : 1));
+    p->zpair = p->Mf % 2 == 0;
+    p->xb_z = shrink(pow2_fit(2 * (size_t)p->M3 * cT, 32), (long)p->Mf * p->Mf / (p->zpair ? 2 : 1));
     for (int c = 0; c < 3; ++c) {
         const size_t cc = c == 0 ? sizeof(Cx<double>) : cT;
         SlabClass &C = p->cls[c];
-        C.rb = shrink(pow2_fit(2 * (size_t)C.ns * cc, 16), (long)C.count * p->Mt);
+        C.rb = shrink(pow2_fit(2 * (size_t)C.ns * cc, 16), (long)C.count * p->Mf);
         C.xb = shrink(pow2_fit(2 * (size_t)C.ns * cc, 32), (long)C.count * C.ns);
     }
     if (2 * (size_t)p->M3 * cT * p->xb_z > 200 * 1024) { delete p; return SE1P_ERR_INVALID_ARG; }
@@ -463,6 +494,7 @@ se1p_status se1p_plan_create(const se1p_params *prm, int n_max, se1p_plan **out)
     }
 
     Alloc A{p};
+    if (const char *e = getenv("SE1P_TEST_FAIL_ALLOC")) A.fail_at = atoi(e);
     se1p_status st = mixed ? alloc_particles<float>(p, A) : alloc_particles<double>(p, A);
     if (st == SE1P_OK) st = mixed ? build_tables<float>(p, A) : build_tables<double>(p, A);
     if (st != SE1P_OK) { free_all(p); delete p; return st; }
@@ -481,7 +513,8 @@ se1p_status se1p_plan_create(const se1p_params *prm, int n_max, se1p_plan **out)
         delete p;
         return SE1P_ERR_CUDA;
     }
-    launch_vico_table(p, 0);
+    if (per3) launch_k3zero_table_3p(p, 0);
+    else launch_vico_table(p, 0);
     if (mixed) launch_symbol_tables<float>(p, 0);
     else launch_symbol_tables<double>(p, 0);
     if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) {
@@ -626,7 +659,7 @@ se1p_status se1p_eval_host(se1p_plan *p, int n, const double *x, const double *q
 
 se1p_status se1p_spread(se1p_plan *p, int n, const double *x, const double *q, double *grid, void *stream)
 {
-    if (!p || bad_n(p, n) || !grid || (n > 0 && (!x || !q))) return SE1P_ERR_INVALID_ARG;
+    if (!p || p->per3 || bad_n(p, n) || !grid || (n > 0 && (!x || !q))) return SE1P_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (p->precision == SE1P_MIXED) {
         launch_pack<float>(p, n, x, q, s);
@@ -644,7 +677,7 @@ se1p_status se1p_spread(se1p_plan *p, int n, const double *x, const double *q, d
 
 se1p_status se1p_fourier(se1p_plan *p, const double *grid_in, double *grid_out, void *stream)
 {
-    if (!p || !grid_in || !grid_out) return SE1P_ERR_INVALID_ARG;
+    if (!p || p->per3 || !grid_in || !grid_out) return SE1P_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (p->precision == SE1P_MIXED) {
         launch_grid_from_double<float>(p, grid_in, p->b.grid, s);
@@ -661,7 +694,7 @@ se1p_status se1p_fourier(se1p_plan *p, const double *grid_in, double *grid_out, 
 se1p_status se1p_gather(se1p_plan *p, int n, const double *x, const double *q, const double *grid, double *phi,
                         double *force, void *stream)
 {
-    if (!p || bad_n(p, n) || !grid || (n > 0 && (!x || !q))) return SE1P_ERR_INVALID_ARG;
+    if (!p || p->per3 || bad_n(p, n) || !grid || (n > 0 && (!x || !q))) return SE1P_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (n == 0) return SE1P_OK;
     if (p->precision == SE1P_MIXED) {

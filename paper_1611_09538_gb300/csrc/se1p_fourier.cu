@@ -362,9 +362,28 @@ __global__ void k_symbol(int ns, int count, int kfirst, double dkap, double dk3,
     }
 }
 
+// ---- triply periodic k3 = 0 scaling table in FP64: 4 pi e^{-(1-eta) kappa^2/4xi^2} / kappa^2 for
+// kappa != 0 and nothing at kappa = 0 (a neutral system in a conducting medium), including 1/(n^2 M3)
+__global__ void k_k3zero_3p(int n, double dkap, double xi, double eta, double norm, double *__restrict__ sym)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * n) return;
+    const double ax = dkap * signed_index(i % n, n), ay = dkap * signed_index(i / n, n);
+    const double k2 = ax * ax + ay * ay;
+    sym[i] = k2 == 0.0 ? 0.0 : norm * 4.0 * kPi * exp(-(1.0 - eta) * k2 / (4.0 * xi * xi)) / k2;
+}
+
 template <typename T> size_t cbytes() { return sizeof(Cx<T>); }
 
 }  // namespace
+
+void launch_k3zero_table_3p(se1p_plan *p, cudaStream_t s)
+{
+    const int n = p->n0;  // = M, the periodic grid
+    const double dkap = 2.0 * kPi / (n * p->geo.h);
+    const double norm = 1.0 / ((double)n * n * p->M3);
+    k_k3zero_3p<<<(n * n + 255) / 256, 256, 0, s>>>(n, dkap, p->geo.xi, p->geo.eta, norm, p->b.sym0);
+}
 
 void launch_vico_table(se1p_plan *p, cudaStream_t s)
 {
@@ -424,7 +443,9 @@ template <typename T> int configure_fourier_kernels(se1p_plan *p)
 
 template <typename T> void launch_fourier(se1p_plan *p, cudaStream_t s)
 {
-    const int Mt = p->Mt, M3 = p->M3, K3 = p->K3;
+    // the transformed grid's free-axis size (the extended grid itself for SE1P, the periodic grid
+    // for triply periodic plans)
+    const int Mt = p->Mf, M3 = p->M3, K3 = p->K3;
     // z forward
     {
         const int xb = p->xb_z;
@@ -432,12 +453,12 @@ template <typename T> void launch_fourier(se1p_plan *p, cudaStream_t s)
         if (p->zpair) {  // xb pencil pairs per CTA
             const int nxc = (Mt / 2 + xb - 1) / xb;
             k_zfwd_pair<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb,
-                                                     make_fastdiv(xb), (const T *)p->b.grid, (Cx<T> *)p->b.zspec,
+                                                     make_fastdiv(xb), (const T *)p->b.gridf, (Cx<T> *)p->b.zspec,
                                                      p->b.slab0_in);
         } else {
             const int nxc = (Mt + xb - 1) / xb;
             k_zfwd<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb,
-                                                make_fastdiv(xb), (const T *)p->b.grid, (Cx<T> *)p->b.zspec,
+                                                make_fastdiv(xb), (const T *)p->b.gridf, (Cx<T> *)p->b.zspec,
                                                 p->b.slab0_in);
         }
     }
@@ -492,12 +513,12 @@ template <typename T> void launch_fourier(se1p_plan *p, cudaStream_t s)
             const int nxc = (Mt / 2 + xb - 1) / xb;
             k_zinv_pair<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb,
                                                      make_fastdiv(xb), (const Cx<T> *)p->b.zspec, p->b.slab0_out,
-                                                     (T *)p->b.grid);
+                                                     (T *)p->b.gridf);
         } else {
             const int nxc = (Mt + xb - 1) / xb;
             k_zinv<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb,
                                                 make_fastdiv(xb), (const Cx<T> *)p->b.zspec, p->b.slab0_out,
-                                                (T *)p->b.grid);
+                                                (T *)p->b.gridf);
         }
     }
 }

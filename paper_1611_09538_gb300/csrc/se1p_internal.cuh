@@ -400,6 +400,7 @@ struct Geo {
     double cs[3];              // cell sizes
     double rc, rc2;
     int nIm;                   // number of k3 > 0 modes in the set I
+    int per3;                  // 1: x and y periodic too (the SE3P comparison method), 0: free (SE1P)
 };
 
 constexpr int kBin = 8;  // spread bin / tile edge in grid points

@@ -47,19 +47,25 @@ constexpr size_t kScratchBytes = kOffCursor + align256(sizeof(int) * kNaMaxCells
 
 static __device__ __align__(256) unsigned char g_na_scratch[kScratchBytes];
 
-// Device address of g_na_scratch on each device, looked up once per device.
+// Device address of g_na_scratch on each device.  It is looked up again on every call made outside
+// stream capture (after cudaDeviceReset the next context may load the module elsewhere); a call
+// during capture uses the address of the last uncaptured call on that device.
 void *g_na_ptr[kNaMaxDevices] = {};
 std::mutex g_na_mutex;
 
-se1p_status na_scratch(void **out)
+se1p_status na_scratch(cudaStream_t s, void **out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) {
         cudaGetLastError();
         return SE1P_ERR_CUDA;
     }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    bool capturing = true;  // if the query itself fails, assume capture and keep the cached address
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess) capturing = cs != cudaStreamCaptureStatusNone;
+    else cudaGetLastError();
     std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
+    if (!capturing || !g_na_ptr[dev]) {
         void *ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_na_scratch) != cudaSuccess || !ptr) {
             cudaGetLastError();
@@ -212,10 +218,10 @@ extern "C" se1p_status se1p_real_space_noalloc(const se1p_params *params, int n,
     for (int i = 0; i < 3; ++i) g.cs[i] = P.L[i] / nc[i];
     g.nbins = 0;
 
-    void *scr = nullptr;
-    se1p_status st = na_scratch(&scr);
-    if (st != SE1P_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    void *scr = nullptr;
+    se1p_status st = na_scratch(s, &scr);
+    if (st != SE1P_OK) return st;
     return P.precision == SE1P_MIXED
                ? na_run<float>(P, g, (unsigned char *)scr, n, x, q, phi, force, s)
                : na_run<double>(P, g, (unsigned char *)scr, n, x, q, phi, force, s);

@@ -47,6 +47,17 @@ __device__ __forceinline__ double grid_coord(double xs, double h, double inv_h, 
     return t;
 }
 
+// Periodic image in [0, L): fmod is exact.
+__device__ __forceinline__ double wrap_periodic(double v, double L)
+{
+    if (v < 0.0 || v >= L) {
+        v = fmod(v, L);
+        if (v < 0.0) v += L;
+        if (v >= L) v = 0.0;
+    }
+    return v;
+}
+
 struct Support {
     int i0[3];
     double t[3];
@@ -84,16 +95,15 @@ __global__ void k_pack(Geo g, int n, const double *__restrict__ x, const double 
             if (!isfinite(pz)) pz = 0.0;
             qq = 0.0;
         }
-        if (px < 0.0 || px >= g.L[0] || py < 0.0 || py >= g.L[1]) {
+        if (g.per3) {  // triply periodic: x and y are wrapped like z
+            px = wrap_periodic(px, g.L[0]);
+            py = wrap_periodic(py, g.L[1]);
+        } else if (px < 0.0 || px >= g.L[0] || py < 0.0 || py >= g.L[1]) {
             flag |= FLAG_OUT_OF_BOX;
             px = fmin(fmax(px, 0.0), g.L[0] * (1.0 - 1e-15));
             py = fmin(fmax(py, 0.0), g.L[1] * (1.0 - 1e-15));
         }
-        if (pz < 0.0 || pz >= g.L[2]) {  // periodic image in [0, L3): fmod is exact
-            pz = fmod(pz, g.L[2]);
-            if (pz < 0.0) pz += g.L[2];
-            if (pz >= g.L[2]) pz = 0.0;
-        }
+        pz = wrap_periodic(pz, g.L[2]);
         const Support s = particle_support(g, px, py, pz);
         const int bx = s.i0[0] / kBin, by = s.i0[1] / kBin, bz = imod(s.i0[2], g.M3) / kBin;
         const int bin = (bz * g.nby + by) * g.nbx + bx;
@@ -777,6 +787,35 @@ __global__ void k_convert(size_t n, const TS *__restrict__ src, TD *__restrict__
         dst[i] = (TD)((double)src[i] * scale);
 }
 
+// Triply periodic plans grid on the extended grid (Mt = M + P, origin -P h/2) and transform the
+// M-periodic grid.  Extended point i sits at (i - P/2) h, periodic point j at j h, so i maps to
+// j = (i - P/2) mod M.  Fold: each periodic point sums its (at most four) extended preimages in a
+// fixed order; unfold: each extended point copies its periodic image.
+template <typename T>
+__global__ void k_fold(int M3, int Mt, int Mf, int sh, const T *__restrict__ ext, T *__restrict__ per)
+{
+    const size_t total = (size_t)M3 * Mf * Mf;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int jx = (int)(i % Mf), jy = (int)((i / Mf) % Mf), z = (int)(i / ((size_t)Mf * Mf));
+        const T *plane = ext + (size_t)z * Mt * Mt;
+        T acc = (T)0;
+        for (int iy = (jy + sh) % Mf; iy < Mt; iy += Mf)
+            for (int ix = (jx + sh) % Mf; ix < Mt; ix += Mf) acc += plane[(size_t)iy * Mt + ix];
+        per[i] = acc;
+    }
+}
+
+template <typename T>
+__global__ void k_unfold(int M3, int Mt, int Mf, int sh, const T *__restrict__ per, T *__restrict__ ext)
+{
+    const size_t total = (size_t)M3 * Mt * Mt;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % Mt), iy = (int)((i / Mt) % Mt), z = (int)(i / ((size_t)Mt * Mt));
+        const int jx = (ix - sh + Mf) % Mf, jy = (iy - sh + Mf) % Mf;  // sh = P/2 <= Mf
+        ext[i] = per[((size_t)z * Mf + jy) * Mf + jx];
+    }
+}
+
 // CTAs for n items of bs threads; kernels with one thread per item and no grid-stride loop
 // pass an uncapped limit
 inline int blocks_for(size_t n, int bs, int cap = 1 << 20)
@@ -900,6 +939,20 @@ template <typename T> void launch_grid_from_double(se1p_plan *p, const double *s
 
 template <typename T> int configure_particle_kernels() { return 0; }
 
+template <typename T> void launch_fold(se1p_plan *p, cudaStream_t s)
+{
+    const size_t n = (size_t)p->M3 * p->Mf * p->Mf;
+    k_fold<T><<<blocks_for(n, 256, 152 * 16), 256, 0, s>>>(p->M3, p->Mt, p->Mf, p->geo.P / 2, (const T *)p->b.grid,
+                                                           (T *)p->b.gridf);
+}
+
+template <typename T> void launch_unfold(se1p_plan *p, cudaStream_t s)
+{
+    const size_t n = (size_t)p->M3 * p->Mt * p->Mt;
+    k_unfold<T><<<blocks_for(n, 256, 152 * 16), 256, 0, s>>>(p->M3, p->Mt, p->Mf, p->geo.P / 2,
+                                                             (const T *)p->b.gridf, (T *)p->b.grid);
+}
+
 #define SE1P_INST(T)                                                                                        \
     template void launch_pack<T>(se1p_plan *, int, const double *, const double *, cudaStream_t, int);     \
     template void launch_sort_scatter<T>(se1p_plan *, int, cudaStream_t);                                   \
@@ -907,7 +960,9 @@ template <typename T> int configure_particle_kernels() { return 0; }
     template void launch_gather<T>(se1p_plan *, int, const void *, double *, double *, int, cudaStream_t);  \
     template void launch_grid_to_double<T>(se1p_plan *, const void *, double *, double, cudaStream_t);           \
     template void launch_grid_from_double<T>(se1p_plan *, const double *, void *, cudaStream_t);           \
-    template int configure_particle_kernels<T>();
+    template int configure_particle_kernels<T>();                                                          \
+    template void launch_fold<T>(se1p_plan *, cudaStream_t);                                                \
+    template void launch_unfold<T>(se1p_plan *, cudaStream_t);
 SE1P_INST(float)
 SE1P_INST(double)
 #undef SE1P_INST

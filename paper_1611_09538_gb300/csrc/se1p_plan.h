@@ -25,6 +25,7 @@ struct SlabClass {
 
 struct Buffers {
     void *grid = nullptr;        // T [M3][Mt][Mt]
+    void *gridf = nullptr;       // T [M3][Mf][Mf] periodic grid of the FFTs (triply periodic plans; else = grid)
     void *zspec = nullptr;       // Cx<T> [K3][Mt][Mt]  (k3 = 0 entry unused)
     double *slab0_in = nullptr;  // k3 = 0 coefficient of H, [Mt][Mt]
     double *slab0_out = nullptr; // k3 = 0 coefficient of Ht, [Mt][Mt]
@@ -62,6 +63,10 @@ struct se1p_plan {
     int precision = 0;
     int device = 0;
     int Mt = 0, M3 = 0, K3 = 0, n0 = 0, nI = 0, nl = 0;
+    // free-axis size of the transformed grid: Mt for SE1P; M for triply periodic plans, whose gridding
+    // runs on the Mt = M + P extended grid and is folded onto the M-periodic grid before the FFTs
+    int Mf = 0;
+    bool per3 = false;
     se1p::FftDesc fd_z{};
     int xb_z = 1;      // z passes: pencils per CTA, or pencil pairs per CTA when zpair
     bool zpair = false;  // Mt even: the z passes transform two real pencils as one complex pencil
@@ -101,11 +106,15 @@ template <typename T>
 void launch_grid_to_double(se1p_plan *p, const void *src, double *dst, double scale, cudaStream_t s);
 template <typename T> void launch_grid_from_double(se1p_plan *p, const double *src, void *dst, cudaStream_t s);
 template <typename T> int configure_particle_kernels();
+// triply periodic plans: fold the extended spread grid onto the periodic grid, and back
+template <typename T> void launch_fold(se1p_plan *p, cudaStream_t s);
+template <typename T> void launch_unfold(se1p_plan *p, cudaStream_t s);
 
 // ---- se1p_fourier.cu
 template <typename T> void launch_fourier(se1p_plan *p, cudaStream_t s);
 template <typename T> int configure_fourier_kernels(se1p_plan *p);
 void launch_vico_table(se1p_plan *p, cudaStream_t s);
+void launch_k3zero_table_3p(se1p_plan *p, cudaStream_t s);
 template <typename T> void launch_symbol_tables(se1p_plan *p, cudaStream_t s);
 
 // ---- se1p_real.cu

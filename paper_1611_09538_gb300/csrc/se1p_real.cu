@@ -88,20 +88,30 @@ template <typename T> struct __align__(sizeof(T) == 4 ? 16 : 32) PairRec {
 
 // Displacement target - source from hi + lo parts.  Each hi difference is one
 // rounding of a difference (exact when the two are within a factor 2, Sterbenz),
-// the lo parts restore the FP64 coordinates to ~1e-15.  In FP64 only z carries a
-// lo part (the rounding error of the image shift).
+// the lo parts restore the FP64 coordinates to ~1e-15.  In FP64 the lo parts hold
+// only the rounding errors of image shifts: z always, x and y for triply periodic plans.
 template <typename T>
-__device__ __forceinline__ void displacement(const PairRec<T> &a, const PairRec<T> &c, T &dx, T &dy, T &dz)
+__device__ __forceinline__ void displacement(const PairRec<T> &a, const PairRec<T> &c, T &dx, T &dy, T &dz, bool per3)
 {
     dx = a.xh - c.xh;
     dy = a.yh - c.yh;
     dz = a.zh - c.zh;
-    if constexpr (sizeof(T) < sizeof(double)) {
+    if (sizeof(T) < sizeof(double) || per3) {
         dx += a.xl - c.xl;
         dy += a.yl - c.yl;
     }
     dz += a.zl - c.zl;
 }
+
+// v + shift as hi + lo: Fast2Sum (|sh| >= |v| whenever sh != 0, since v lies in [0, L) and sh is a
+// whole number of periods) gives the rounding error of the hi sum exactly
+template <typename T> __device__ __forceinline__ void shifted(T vh, T vl, T sh, T shl, T &oh, T &ol)
+{
+    oh = sh + vh;
+    ol = (vl + shl) + (vh - (oh - sh));
+}
+
+__device__ __forceinline__ int floor_div(int a, int m) { return a >= 0 ? a / m : -((-a + m - 1) / m); }
 
 // Contribution of one source of charge qs at displacement d (Eq. 2.2 and its
 // gradient, Eq. 3.22), added to (ph, fx, fy, fz).  Pairs with r = 0 (the target
@@ -144,7 +154,7 @@ __device__ __forceinline__ void pair_terms(T dx, T dy, T dz, T qs, T rc2, T xi, 
 //            r <= rc test and the pair terms, branch-free.
 // (Spreading the marks of busy lanes over idle ones through shared memory was
 // measured slower: the bookkeeping per pair costs more than the idle lanes.)
-template <typename T, int SPLIT>
+template <typename T, int SPLIT, bool PER3>
 __global__ void __launch_bounds__(32 * kRealWarps) k_real(Geo g, int n, const int *__restrict__ cell_start,
                                                           const CellRec<T> *__restrict__ cells,
                                                           const int *__restrict__ cell_key,
@@ -200,8 +210,12 @@ __global__ void __launch_bounds__(32 * kRealWarps) k_real(Geo g, int n, const in
     const float rbox2 = rbox * rbox;
     const int Sx = (int)ceil(g.rc / g.cs[0] - 1e-9), Sy = (int)ceil(g.rc / g.cs[1] - 1e-9),
               Sz = (int)ceil(g.rc / g.cs[2] - 1e-9);
-    const int nx_lo = max(cx0 - Sx, 0), nx_hi = min(cx1 + Sx, g.ncx - 1);
-    const int ny_lo = max(cy0 - Sy, 0), ny_hi = min(cy1 + Sy, g.ncy - 1);
+    // unwrapped cell ranges: clamped to the box on the free axes (SE1P), periodic images on every
+    // axis of a triply periodic plan; an x range that crosses the box edge splits into segments
+    constexpr bool per3 = PER3;  // triply periodic plan (g.per3)
+    const int nx_lo = per3 ? cx0 - Sx : max(cx0 - Sx, 0), nx_hi = per3 ? cx1 + Sx : min(cx1 + Sx, g.ncx - 1);
+    const int ny_lo = per3 ? cy0 - Sy : max(cy0 - Sy, 0), ny_hi = per3 ? cy1 + Sy : min(cy1 + Sy, g.ncy - 1);
+    const int wx0 = per3 ? floor_div(nx_lo, g.ncx) : 0, nseg = per3 ? floor_div(nx_hi, g.ncx) - wx0 + 1 : 1;
     const T xi = (T)g.xi, rc2 = (T)g.rc2;
     const T two_xi_sqpi = (T)(2.0 * g.xi / sqrt(kPi));
     const T xi2 = (T)(g.xi * g.xi);
@@ -249,7 +263,7 @@ __global__ void __launch_bounds__(32 * kRealWarps) k_real(Geo g, int n, const in
                 const int j = (k0 + __ffs(m) - 1) * kLanesPerTarget + half;
                 m &= m - 1u;
                 T dx, dy, dz;
-                displacement(me, cl[j], dx, dy, dz);
+                displacement(me, cl[j], dx, dy, dz, per3);
                 pair_terms(dx, dy, dz, cl[j].q, rc2, xi, xi2, two_xi_sqpi, pphi, pfx, pfy, pfz);
             }
         };
@@ -264,23 +278,33 @@ __global__ void __launch_bounds__(32 * kRealWarps) k_real(Geo g, int n, const in
     };
 
     const int nyr = ny_hi - ny_lo + 1;
-    const int nrows = (cz1 + Sz - (cz0 - Sz) + 1) * max(nyr, 0);
+    const int nrows = (cz1 + Sz - (cz0 - Sz) + 1) * max(nyr, 0) * nseg;
     for (int rr = part; rr < nrows; rr += SPLIT) {
-        const int nzu = cz0 - Sz + rr / nyr, ny = ny_lo + rr % nyr;
-        const int wrap = nzu >= 0 ? nzu / g.ncz : -((-nzu + g.ncz - 1) / g.ncz);
-        const int nz = nzu - wrap * g.ncz;
+        const int seg = rr % nseg, ryz = rr / nseg;
+        const int nzu = cz0 - Sz + ryz / nyr, nyu = ny_lo + ryz % nyr;
+        const int wrap = floor_div(nzu, g.ncz), wy = per3 ? floor_div(nyu, g.ncy) : 0, wx = wx0 + seg;
+        const int nz = nzu - wrap * g.ncz, ny = nyu - wy * g.ncy;
         const double shd = wrap * g.L[2];
         const T sh = (T)shd, shl = (T)(shd - (double)sh);
         const float shf = (float)shd;
+        // x and y image shifts (zero for SE1P)
+        const double sxd = per3 ? wx * g.L[0] : 0.0, syd = per3 ? wy * g.L[1] : 0.0;
+        const T sxh = (T)sxd, sxl = (T)(sxd - (double)sxh), syh = (T)syd, syl = (T)(syd - (double)syh);
+        const float sxf = (float)sxd, syf = (float)syd;
+        const int xa = per3 ? max(nx_lo, wx * g.ncx) - wx * g.ncx : nx_lo;
+        const int xb = per3 ? min(nx_hi, wx * g.ncx + g.ncx - 1) - wx * g.ncx : nx_hi;
         const int row = (nz * g.ncy + ny) * g.ncx;
-        const int sbeg = cell_start[row + nx_lo], send = cell_start[row + nx_hi + 1];
+        const int sbeg = cell_start[row + xa], send = cell_start[row + xb + 1];
         for (int s0 = sbeg; s0 < send; s0 += 32) {
             const int si = s0 + lane;
             bool keep = false;
             CellRec<T> rec;
+            float sx = 0.f, sy = 0.f, sz = 0.f;
             if (si < send) {
                 rec = cells[si];
-                const float sx = (float)rec.xh, sy = (float)rec.yh, sz = (float)rec.zh + shf;
+                sx = (float)rec.xh + sxf;
+                sy = (float)rec.yh + syf;
+                sz = (float)rec.zh + shf;
                 const float ex = fmaxf(fmaxf(bx0 - sx, sx - bx1), 0.0f);
                 const float ey = fmaxf(fmaxf(by0 - sy, sy - by1), 0.0f);
                 const float ez = fmaxf(fmaxf(bz0 - sz, sz - bz1), 0.0f);
@@ -289,23 +313,22 @@ __global__ void __launch_bounds__(32 * kRealWarps) k_real(Geo g, int n, const in
             const unsigned bal = __ballot_sync(full, keep);
             if (keep) {
                 const int pos = ncand + __popc(bal & lt_mask);
-                // z + shift as hi + lo: Fast2Sum (|sh| > |zh| whenever sh != 0) gives the
-                // rounding error of the hi sum exactly
-                const T zs = sh + rec.zh;
-                const T zerr = rec.zh - (zs - sh);
                 PairRec<T> c;
-                c.xh = rec.xh;
-                c.yh = rec.yh;
-                c.zh = zs;
+                shifted(rec.zh, rec.zl, sh, shl, c.zh, c.zl);
+                if constexpr (per3) {
+                    shifted(rec.xh, rec.xl, sxh, sxl, c.xh, c.xl);
+                    shifted(rec.yh, rec.yl, syh, syl, c.yh, c.yl);
+                } else {
+                    c.xh = rec.xh;
+                    c.xl = rec.xl;
+                    c.yh = rec.yh;
+                    c.yl = rec.yl;
+                }
                 c.q = rec.q;
-                c.xl = rec.xl;
-                c.yl = rec.yl;
-                c.zl = (rec.zl + shl) + zerr;
                 c.pad = (T)0;
                 cl[pos] = c;
                 if constexpr (sizeof(T) != 4)
-                    cposd[sizeof(T) == 4 ? 0 : wib][sizeof(T) == 4 ? 0 : pos] =
-                        make_float4((float)rec.xh, (float)rec.yh, (float)rec.zh + shf, (float)rec.q);
+                    cposd[sizeof(T) == 4 ? 0 : wib][sizeof(T) == 4 ? 0 : pos] = make_float4(sx, sy, sz, (float)rec.q);
             }
             ncand += __popc(bal);
             if (ncand >= 64) {
@@ -348,14 +371,16 @@ void launch_real_space(se1p_plan *p, int n, const int *cell_key, double *phi, do
     // expected neighbours of a target within rc at uniform density
     const double neighbours = n / (g.L[0] * g.L[1] * g.L[2]) * 4.0 / 3.0 * kPi * g.rc * g.rc * g.rc;
     const int groups = (n + kRealTargets - 1) / kRealTargets;
+    const int *starts = p->b.starts + g.nbins + 1;
+    const CellRec<T> *cells = (const CellRec<T> *)p->b.cells;
     if (neighbours >= kRealSplitNeighbours) {
-        const int warps = groups * 4;
-        k_real<T, 4><<<(warps + kRealWarps - 1) / kRealWarps, 32 * kRealWarps, 0, s>>>(
-            g, n, p->b.starts + g.nbins + 1, (const CellRec<T> *)p->b.cells, cell_key, phi, frc, accumulate);
+        const int blocks = (groups * 4 + kRealWarps - 1) / kRealWarps;
+        if (g.per3) k_real<T, 4, true><<<blocks, 32 * kRealWarps, 0, s>>>(g, n, starts, cells, cell_key, phi, frc, accumulate);
+        else k_real<T, 4, false><<<blocks, 32 * kRealWarps, 0, s>>>(g, n, starts, cells, cell_key, phi, frc, accumulate);
     } else {
-        const int warps = groups * 2;
-        k_real<T, 2><<<(warps + kRealWarps - 1) / kRealWarps, 32 * kRealWarps, 0, s>>>(
-            g, n, p->b.starts + g.nbins + 1, (const CellRec<T> *)p->b.cells, cell_key, phi, frc, accumulate);
+        const int blocks = (groups * 2 + kRealWarps - 1) / kRealWarps;
+        if (g.per3) k_real<T, 2, true><<<blocks, 32 * kRealWarps, 0, s>>>(g, n, starts, cells, cell_key, phi, frc, accumulate);
+        else k_real<T, 2, false><<<blocks, 32 * kRealWarps, 0, s>>>(g, n, starts, cells, cell_key, phi, frc, accumulate);
     }
 }
 

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libse1p.so")
 
 SE1P_FP64 = 0
 SE1P_MIXED = 1
+SE1P_FLAG_TRIPLY_PERIODIC = 1  # params.flags: the triply periodic comparison method (SE3P)
 
 STATUS = {
     0: "SE1P_OK", 1: "SE1P_ERR_INVALID_ARG", 2: "SE1P_ERR_NOT_NEUTRAL", 3: "SE1P_ERR_OUT_OF_BOX",
@@ -33,7 +34,7 @@ EXPORTS = (
     "se1p_spread", "se1p_fourier", "se1p_gather", "se1p_real_space", "se1p_plan_set_profiling",
     "se1p_plan_stage_times", "se1p_plan_sync_status", "se1p_real_space_noalloc", "se1p_status_string",
     "se1p_autotune", "se1p_batch_create", "se1p_batch_destroy", "se1p_batch_eval", "se1p_batch_sync_status",
-    "se1p_batch_plan",
+    "se1p_batch_plan", "se1p_measure_fma_peak",
 )
 
 STAGES = ("pack", "spread", "fourier", "gather", "real", "final")
@@ -107,6 +108,7 @@ def load(path: str | None = None):
     lib.se1p_batch_sync_status.argtypes = [vp, vp]
     lib.se1p_batch_plan.argtypes = [vp, i]
     lib.se1p_batch_plan.restype = vp
+    lib.se1p_measure_fma_peak.argtypes = [i, ctypes.POINTER(d), ctypes.POINTER(i)]
     for name in EXPORTS:
         if name not in ("se1p_status_string", "se1p_batch_plan"):
             getattr(lib, name).restype = i
@@ -140,7 +142,7 @@ def _stream(stream):
 
 
 def make_params(L, xi, M, P, *, Mt=0, n0=0, nI=0, nl=-1, s0=0.0, sl=0.0, rc=0.0, tol=0.0,
-                precision=SE1P_FP64) -> se1p_params:
+                precision=SE1P_FP64, flags=0) -> se1p_params:
     prm = se1p_params()
     prm.L[:] = [float(v) for v in L]
     prm.xi = float(xi)
@@ -149,7 +151,7 @@ def make_params(L, xi, M, P, *, Mt=0, n0=0, nI=0, nl=-1, s0=0.0, sl=0.0, rc=0.0,
     prm.Mt, prm.n0, prm.nI, prm.nl = int(Mt), int(n0), int(nI), int(nl)
     prm.s0, prm.sl, prm.rc, prm.tol = float(s0), float(sl), float(rc if rc is not None else 0.0), float(tol)
     prm.precision = int(precision)
-    prm.flags = 0
+    prm.flags = int(flags)
     return prm
 
 
@@ -228,6 +230,16 @@ def se1p_real_space_noalloc(params: se1p_params, n, x, q, phi, force, stream=Non
     n <= 16384; concurrent calls must be serialised by the caller)."""
     _check(load().se1p_real_space_noalloc(ctypes.byref(params), int(n), _ptr(x), _ptr(q), _ptr(phi),
                                           _ptr(force), _stream(stream)), "se1p_real_space_noalloc")
+
+
+def se1p_measure_fma_peak(precision) -> tuple[float, int]:
+    """Measured FMA throughput (TFLOP/s, FP32 for SE1P_MIXED, FP64 for SE1P_FP64) of the
+    current device and its multiprocessor count."""
+    tf = ctypes.c_double()
+    sms = ctypes.c_int()
+    _check(load().se1p_measure_fma_peak(int(precision), ctypes.byref(tf), ctypes.byref(sms)),
+           "se1p_measure_fma_peak")
+    return tf.value, sms.value
 
 
 def se1p_status_string(code: int) -> str:

@@ -56,6 +56,10 @@ def test_status_strings(lib):
     dict(L=(1, 1, 1), xi=8.0, M=(32, 32, 32), P=16, Mt=40), # Mt < M + P
     dict(L=(1, 1, 1), xi=8.0, M=(32, 32, 32), P=16, n0=143),  # n0 not 7-smooth
     dict(L=(1, 1, 1), xi=8.0, M=(32, 32, 32), P=16, rc=2.0),  # rc > L3
+    dict(L=(1, 1, 1), xi=8.0, M=(32, 32, 32), P=16, flags=2),  # unknown flag
+    dict(L=(1, 1, 1), xi=8.0, M=(32, 32, 32), P=15, flags=1),  # triply periodic: odd P
+    dict(L=(1, 1, 1), xi=8.0, M=(22, 22, 32), P=16, flags=1),  # triply periodic: M not 7-smooth
+    dict(L=(0.5, 0.5, 2), xi=8.0, M=(32, 32, 64), P=16, rc=0.8, flags=1),  # triply periodic: rc > L1
 ])
 def test_invalid_parameters_rejected_on_host(lib, bad):
     kw = dict(bad)

@@ -106,6 +106,7 @@ typedef struct {
     double eta, etaz;       /* Gaussian shape eta = P xi^2 h^2/(c^2 pi), c = 0.95 (Eq. 3.3) */
     double R;               /* truncation radius of the 2-D kernel, sqrt(2) Mt h          */
     int cells[3];           /* real-space cell list dimensions                            */
+    int features;           /* bit 0: the z forward pass loads its pencils by bulk tensor copies */
     size_t workspace_bytes; /* device memory owned by the plan                            */
 } se1p_plan_info;
 

@@ -495,6 +495,8 @@ se1p_status se1p_plan_create(const se1p_params *prm, int n_max, se1p_plan **out)
 
     Alloc A{p};
     if (const char *e = getenv("SE1P_TEST_FAIL_ALLOC")) A.fail_at = atoi(e);
+    // polls of the bounded device waits; SE1P_TEST_SPIN_LIMIT (tests only) makes them give up early
+    if (const char *e = getenv("SE1P_TEST_SPIN_LIMIT")) p->spin_limit = atoll(e);
     se1p_status st = mixed ? alloc_particles<float>(p, A) : alloc_particles<double>(p, A);
     if (st == SE1P_OK) st = mixed ? build_tables<float>(p, A) : build_tables<double>(p, A);
     if (st != SE1P_OK) { free_all(p); delete p; return st; }
@@ -556,6 +558,7 @@ se1p_status se1p_plan_get_info(const se1p_plan *p, se1p_plan_info *info)
     info->cells[0] = p->geo.ncx;
     info->cells[1] = p->geo.ncy;
     info->cells[2] = p->geo.ncz;
+    info->features = p->tma_zfwd ? 1 : 0;
     info->workspace_bytes = p->bytes;
     return SE1P_OK;
 }

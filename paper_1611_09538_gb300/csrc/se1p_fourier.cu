@@ -82,26 +82,51 @@ template <typename T> struct Pair2;
 template <> struct Pair2<float> { using type = float2; };
 template <> struct Pair2<double> { using type = double2; };
 
+// With a tensor map (tma != 0) the CTA's M3 x 2 xp real values arrive by bulk tensor copies (boxes of
+// 2 xp x 1 x zbox values of the [z][y][x] grid, x beyond the row filled with zeros) that land in
+// shared memory exactly as the complex pencils: value (z, x = 2 (j0 + pp) + r) at a[z xp + pp], part r.
+// The wait on them is bounded (spin_limit polls); a CTA that gives up records FLAG_TIMEOUT in *status,
+// waits for its copies to land (bounded as well) and returns without writing results.
 template <typename T>
 __global__ void k_zfwd_pair(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restrict__ tw, int xp, FastDiv fxp,
-                            const T *__restrict__ grid, Cx<T> *__restrict__ zspec, double *__restrict__ slab0)
+                            const T *__restrict__ grid, Cx<T> *__restrict__ zspec, double *__restrict__ slab0,
+                            const __grid_constant__ CUtensorMap tm, int tma, int zbox, int *__restrict__ status,
+                            long long spin_limit)
 {
     using V2 = typename Pair2<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long bar;
     Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
     Cx<T> *b = a + (size_t)M3 * xp;
     const int npair = Mt / 2, nxc = (npair + xp - 1) / xp;
     const int y = blockIdx.x / nxc, j0 = (blockIdx.x % nxc) * xp;
-    for (int e = threadIdx.x; e < M3 * xp; e += blockDim.x) {
-        const int z = fdiv(e, fxp), pp = e - z * xp, j = j0 + pp;
-        Cx<T> v = cx<T>((T)0, (T)0);
-        if (j < npair) {
-            const V2 h = *reinterpret_cast<const V2 *>(grid + ((size_t)z * Mt + y) * Mt + 2 * j);
-            v = cx<T>(h.x, h.y);
+    if (tma) {
+        const unsigned bar_a = smem_addr(&bar);
+        if (threadIdx.x == 0) {
+            mbar_init(bar_a, 1);
+            mbar_expect_tx(bar_a, (unsigned)((size_t)M3 * xp * sizeof(Cx<T>)));
+            for (int z0 = 0; z0 < M3; z0 += zbox) tma_load_3d(smem_addr(a + (size_t)z0 * xp), &tm, 2 * j0, y, z0, bar_a);
         }
-        a[e] = v;
+        __syncthreads();  // the barrier is initialised before anyone polls it
+        const bool late = !mbar_wait(bar_a, 0, spin_limit);
+        if (__syncthreads_or(late)) {
+            if (threadIdx.x == 0) atomicOr(status, FLAG_TIMEOUT);
+            mbar_wait(bar_a, 0, kDrainPolls);
+            __syncthreads();
+            return;
+        }
+    } else {
+        for (int e = threadIdx.x; e < M3 * xp; e += blockDim.x) {
+            const int z = fdiv(e, fxp), pp = e - z * xp, j = j0 + pp;
+            Cx<T> v = cx<T>((T)0, (T)0);
+            if (j < npair) {
+                const V2 h = *reinterpret_cast<const V2 *>(grid + ((size_t)z * Mt + y) * Mt + 2 * j);
+                v = cx<T>(h.x, h.y);
+            }
+            a[e] = v;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     // k3 = 0: each pencil's z sum to FP64 accuracy, as in k_zfwd (real part: pencil 2j, imaginary: 2j + 1)
     {
         __shared__ double part[2][256];
@@ -421,8 +446,45 @@ template <typename K> cudaError_t allow_max_dynamic_smem(K kernel, int maxsm)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm - (int)fa.sharedSizeBytes);
 }
 
+// Tensor map of the z forward pass: the [z][y][x] grid of T (x fastest), boxes of 2 xb x 1 x zbox values.
+// Used when the pencil pairs' box and the row stride are multiples of 16 bytes (the tensor-copy
+// alignment rules: every copied x offset 2 j0 is then a multiple of 16 bytes too) and zbox, the largest
+// divisor of M3 up to 256 (the box limit per dimension), gives whole boxes.
+template <typename T> void make_zfwd_tensor_map(se1p_plan *p)
+{
+    p->tma_zfwd = false;
+    const int Mt = p->Mf, M3 = p->M3, xp = p->xb_z;
+    if (!p->zpair || (Mt * sizeof(T)) % 16 != 0 || (2 * xp * sizeof(T)) % 16 != 0 || 2 * xp > 256) return;
+    int zbox = 1;
+    for (int v = 1; v <= 256 && v <= M3; ++v)
+        if (M3 % v == 0) zbox = v;
+    if (zbox < 8) return;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return;
+    }
+    using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    const cuuint64_t dims[3] = {(cuuint64_t)Mt, (cuuint64_t)Mt, (cuuint64_t)M3};
+    const cuuint64_t strides[2] = {(cuuint64_t)Mt * sizeof(T), (cuuint64_t)Mt * Mt * sizeof(T)};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * xp), 1u, (cuuint32_t)zbox};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    const CUresult r = reinterpret_cast<Encode>(fn)(
+        &p->tm_zfwd, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, p->b.gridf,
+        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return;
+    p->tma_zfwd = true;
+    p->tma_zbox = zbox;
+}
+
 template <typename T> int configure_fourier_kernels(se1p_plan *p)
 {
+    make_zfwd_tensor_map<T>(p);
     int dev;
     cudaGetDevice(&dev);
     int maxsm = 0;
@@ -454,7 +516,8 @@ template <typename T> void launch_fourier(se1p_plan *p, cudaStream_t s)
             const int nxc = (Mt / 2 + xb - 1) / xb;
             k_zfwd_pair<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb,
                                                      make_fastdiv(xb), (const T *)p->b.gridf, (Cx<T> *)p->b.zspec,
-                                                     p->b.slab0_in);
+                                                     p->b.slab0_in, p->tm_zfwd, p->tma_zfwd ? 1 : 0, p->tma_zbox,
+                                                     p->b.status, p->spin_limit);
         } else {
             const int nxc = (Mt + xb - 1) / xb;
             k_zfwd<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb,

@@ -5,6 +5,7 @@
 // at x + P h/2 on [0, Mt h)), z is periodic with M3 points.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -136,6 +137,46 @@ template <typename T> __device__ __forceinline__ Cx<T> tw_mul(Cx<T> v, Tw<T> w, 
         return cx<float>(re, im);
     }
 }
+
+// ------------------------------------------------------------------ bulk tensor copies (TMA)
+// One CTA-local mbarrier tracks the bytes of the tensor copies a CTA issues; every wait on it is
+// bounded by an iteration count, after which the caller records FLAG_TIMEOUT and drains.
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor-copy unit
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// true when the phase completed within `limit` polls (each poll may suspend the thread briefly)
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase, long long limit)
+{
+    for (long long it = 0; it < limit; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// 3-D tiled copy global -> shared of the box at (x, y, z) of tensor map `tm`, completing on `bar`
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const void *tm, int x, int y, int z, unsigned bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(tm)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+constexpr long long kDrainPolls = 1ll << 24;  // bound of the wait for copies still in flight after a timeout
 
 // ------------------------------------------------------------------ FFT descriptor
 // A length-n transform factored into radices (applied first to last).  The

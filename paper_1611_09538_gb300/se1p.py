@@ -60,7 +60,8 @@ class se1p_plan_info(ctypes.Structure):
         ("Mt", ctypes.c_int), ("M3", ctypes.c_int), ("n0", ctypes.c_int), ("nI", ctypes.c_int),
         ("nl", ctypes.c_int), ("n_I_modes", ctypes.c_int), ("P", ctypes.c_int), ("precision", ctypes.c_int),
         ("h", ctypes.c_double), ("hz", ctypes.c_double), ("eta", ctypes.c_double), ("etaz", ctypes.c_double),
-        ("R", ctypes.c_double), ("cells", ctypes.c_int * 3), ("workspace_bytes", ctypes.c_size_t),
+        ("R", ctypes.c_double), ("cells", ctypes.c_int * 3), ("features", ctypes.c_int),
+        ("workspace_bytes", ctypes.c_size_t),
     ]
 
 

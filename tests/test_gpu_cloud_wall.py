@@ -7,8 +7,12 @@ Vico-truncated k3 = 0 mode and the upsampling must handle.  At 24 sampled target
   * parity: FP64 phi and F equal the restatement of Algorithm 1 (k-space) plus the direct
     real-space and self terms, element by element (1e-10 of the largest value);
   * accuracy of the method at these shapes: the k-space force (GPU total minus GPU real space)
-    against the direct Ewald1P k-space sums.  The restatement itself gives 1.0e-4 rms here
-    (Table 6.2 prints 1.7e-5 for its own, unpublished, cloud-wall system), bound 2e-4;
+    against the direct Ewald1P k-space sums: 1.0e-4 rms on the stand-in, bound 1.5e-4.  Table 6.2
+    prints 1.7e-5 for its own, unpublished, cloud-wall system.  The gap is the stand-in's charge
+    distribution, not the method: a uniform system at the same N, L, M, P, xi, s_l and n_l gives
+    2.2e-5 (second test), and on the stand-in the error sits on the dense charges (wall 1.2e-4,
+    cloud 8e-5 rms; the cloud is ~30x denser than N/L^3 = 0.3, the wall ~20x), since the
+    truncation error of a charge grows with the charge density around it;
   * mixed FP32/FP64 against FP64: relative rms <= 1e-6 for phi and F."""
 import numpy as np
 import pytest
@@ -65,6 +69,29 @@ def test_cloud_wall_row_19200():
     kerr = np.sqrt(np.mean(np.sum((Fk - (fk[:, 1] + fk[:, 2])) ** 2, axis=1)))
     print(f"cloud-wall N={N}: k-space rms force error {kerr:.2e}; mixed vs FP64 phi "
           f"{rel(out[1][0], phi):.2e}, F {rel(out[1][1], F):.2e}")
-    assert kerr < 2e-4
+    assert kerr < 1.5e-4
     assert rel(out[se1p.SE1P_MIXED][0], phi) < 1e-6
     assert rel(out[se1p.SE1P_MIXED][1], F) < 1e-6
+
+
+def test_uniform_system_at_the_table_6_2_shapes():
+    """The N = 19 200 row's parameters (L = 40, M = 64, P = 12, xi = 0.7186, s_l = 2, n_l = 4) on
+    uniform +-1 charges at the same density N/L^3 = 0.3: the k-space rms force error against the
+    direct sums is at the level Table 6.2 prints (1.7e-5), bound 3.4e-5 (2x)."""
+    N, L, M, nl, xi, P, rc = 19200, 40.0, 64, 4, 0.7186, 12, 5.0
+    Mt, n0, nI = 80, 192, 160
+    x, q = inputs.uniform_alternating(N, (L, L, L), seed=19)
+    xd, qd = torch.as_tensor(x, device="cuda"), torch.as_tensor(q, device="cuda")
+    plan = se1p.Plan((L, L, L), xi, (M, M, M), P, N, Mt=Mt, n0=n0, nI=nI, nl=nl, rc=rc, precision=se1p.SE1P_FP64)
+    r = plan.eval(xd, qd)
+    pr = torch.zeros(N, dtype=torch.float64, device="cuda")
+    fr = torch.zeros((N, 3), dtype=torch.float64, device="cuda")
+    se1p.se1p_real_space(plan.handle, N, xd, qd, pr, fr)
+    torch.cuda.synchronize()
+    F, Freal = r.force.cpu().numpy(), fr.cpu().numpy()
+    plan.close()
+    tg = np.random.default_rng(9).choice(N, size=48, replace=False)
+    pk, fk = direct.ewald1p_parts(x, q, L, xi, -1.0, targets=tg)
+    kerr = np.sqrt(np.mean(np.sum((F[tg] - Freal[tg] - (fk[:, 1] + fk[:, 2])) ** 2, axis=1)))
+    print(f"uniform N={N}: k-space rms force error {kerr:.2e} (Table 6.2: 1.717e-05)")
+    assert kerr < 3.4e-5

@@ -17,19 +17,8 @@ constexpr int kRealWarps = 4;  // warps per CTA (warps work independently)
 // rc = 0.15 (~1400 expected neighbours): 1.528 ms with four, 1.543 with two; N = 10^6 in [1,1,8],
 // rc = 0.09 (~380): 12.42 ms with four, 12.32 with two.
 constexpr double kRealSplitNeighbours = 800.0;
-#ifndef SE1P_REAL_FIXED64
-#define SE1P_REAL_FIXED64 0
-#endif
-#ifndef SE1P_REAL_PREFETCH
-#define SE1P_REAL_PREFETCH 0
-#endif
-#ifndef SE1P_REAL_MINB
-#define SE1P_REAL_MINB 1
-#endif
-#ifndef SE1P_REAL_UNROLL
-#define SE1P_REAL_UNROLL 32
-#endif
-constexpr int kPhase1Unroll = SE1P_REAL_UNROLL;
+// CTAs per SM the FP32 kernel is compiled for (72 registers per thread): with the unrolled candidate
+// test the compiler would take 96 and fit five; seven are faster (C2, stage alone: 0.83 against 0.96 ms)
 constexpr int kCand = 96;      // per-warp candidate list (flushed at >= 64)
 constexpr int kRealTargets = 16;                     // targets per warp
 constexpr int kLanesPerTarget = 32 / kRealTargets;   // lanes sharing a target (alternate candidates)
@@ -167,8 +156,10 @@ __device__ __forceinline__ void pair_terms(T dx, T dy, T dz, T qs, T rc2, T xi, 
 //            r <= rc test and the pair terms, branch-free.
 // (Spreading the marks of busy lanes over idle ones through shared memory was
 // measured slower: the bookkeeping per pair costs more than the idle lanes.)
+constexpr int kRealMinBlocks32 = 7;
+
 template <typename T, int SPLIT, bool PER3>
-__global__ void __launch_bounds__(32 * kRealWarps, SE1P_REAL_MINB) k_real(Geo g, int n, const int *__restrict__ cell_start,
+__global__ void __launch_bounds__(32 * kRealWarps, sizeof(T) == 4 ? kRealMinBlocks32 : 1) k_real(Geo g, int n, const int *__restrict__ cell_start,
                                                           const CellRec<T> *__restrict__ cells,
                                                           const int *__restrict__ cell_key,
                                                           double *__restrict__ phi, double *__restrict__ frc,
@@ -245,13 +236,14 @@ __global__ void __launch_bounds__(32 * kRealWarps, SE1P_REAL_MINB) k_real(Geo g,
     const double lmax = fmax(fmax(g.L[0], g.L[1]), g.L[2]);
     const float rc2wf = (float)((g.rc * (1.0 + 1e-5) + 5e-7 * lmax) * (g.rc * (1.0 + 1e-5) + 5e-7 * lmax));
 
-    auto process = [&](int nc) {
+    auto process = [&](int nc) {  // nc <= 64 candidates in cl[0 .. nc)
         __syncwarp();
-        // phase 1: candidates within rc of this lane's target (float test, widened threshold)
-        unsigned m0 = 0u, m1 = 0u, m2 = 0u;
-#if SE1P_REAL_FIXED64
+        // phase 1: candidates within rc of this lane's target (float test, widened threshold); this
+        // lane's candidate k kLanesPerTarget + half is bit k of its marks.  Always 64 / kLanesPerTarget
+        // tests, unrolled, then the bits beyond nc are cleared (the list past nc holds stale records).
+        unsigned m0 = 0u;
         if (valid) {
-#pragma unroll kPhase1Unroll
+#pragma unroll
             for (int k = 0; k < 64 / kLanesPerTarget; ++k) {
                 const float4 c = cp[(k * kLanesPerTarget + half) * cps];
                 const float dx = mxf - c.x, dy = myf - c.y, dz = mzf - c.z;
@@ -259,29 +251,6 @@ __global__ void __launch_bounds__(32 * kRealWarps, SE1P_REAL_MINB) k_real(Geo g,
             }
             const int nk = (nc - half + kLanesPerTarget - 1) / kLanesPerTarget;
             if (nk < 32) m0 &= (1u << max(nk, 0)) - 1u;
-        }
-        if (false) {
-#else
-        if (valid) {
-#endif
-            // candidate j = k kLanesPerTarget + half is bit k of this lane's marks
-            const int nk = (nc - half + kLanesPerTarget - 1) / kLanesPerTarget;
-            const int n0 = min(nk, 32), n1 = min(nk, 64);
-            for (int k = 0; k < n0; ++k) {
-                const float4 c = cp[(k * kLanesPerTarget + half) * cps];
-                const float dx = mxf - c.x, dy = myf - c.y, dz = mzf - c.z;
-                if (dx * dx + dy * dy + dz * dz <= rc2wf) m0 |= 1u << k;
-            }
-            for (int k = 32; k < n1; ++k) {
-                const float4 c = cp[(k * kLanesPerTarget + half) * cps];
-                const float dx = mxf - c.x, dy = myf - c.y, dz = mzf - c.z;
-                if (dx * dx + dy * dy + dz * dz <= rc2wf) m1 |= 1u << (k - 32);
-            }
-            for (int k = 64; k < nk; ++k) {
-                const float4 c = cp[(k * kLanesPerTarget + half) * cps];
-                const float dx = mxf - c.x, dy = myf - c.y, dz = mzf - c.z;
-                if (dx * dx + dy * dy + dz * dz <= rc2wf) m2 |= 1u << (k - 64);
-            }
         }
         // phase 2: this lane's marks, word by word
         T pphi = 0, pfx = 0, pfy = 0, pfz = 0;
@@ -295,8 +264,6 @@ __global__ void __launch_bounds__(32 * kRealWarps, SE1P_REAL_MINB) k_real(Geo g,
             }
         };
         walk(m0, 0);
-        walk(m1, 32);
-        walk(m2, 64);
         aphi += (double)pphi;
         afx += (double)pfx;
         afy += (double)pfy;
@@ -322,26 +289,12 @@ __global__ void __launch_bounds__(32 * kRealWarps, SE1P_REAL_MINB) k_real(Geo g,
         const int xb = per3 ? min(nx_hi, wx * g.ncx + g.ncx - 1) - wx * g.ncx : nx_hi;
         const int row = (nz * g.ncy + ny) * g.ncx;
         const int sbeg = cell_start[row + xa], send = cell_start[row + xb + 1];
-#if SE1P_REAL_PREFETCH
-        CellRec<T> nxt;
-        bool hn = sbeg + lane < send;
-        if (hn) nxt = cells[sbeg + lane];
-#endif
         for (int s0 = sbeg; s0 < send; s0 += 32) {
             bool keep = false;
-#if SE1P_REAL_PREFETCH
-            const CellRec<T> rec = nxt;
-            const bool have = hn;
-            if (s0 + 32 < send) {
-                hn = s0 + 32 + lane < send;
-                if (hn) nxt = cells[s0 + 32 + lane];
-            }
-#else
             const int si = s0 + lane;
             const bool have = si < send;
             CellRec<T> rec;
             if (have) rec = cells[si];
-#endif
             float sx = 0.f, sy = 0.f, sz = 0.f;
             if (have) {
                 sx = (float)rec.xh + sxf;
@@ -373,7 +326,6 @@ __global__ void __launch_bounds__(32 * kRealWarps, SE1P_REAL_MINB) k_real(Geo g,
                     cposd[sizeof(T) == 4 ? 0 : wib][sizeof(T) == 4 ? 0 : pos] = make_float4(sx, sy, sz, (float)rec.q);
             }
             ncand += __popc(bal);
-#if SE1P_REAL_FIXED64
             if (ncand >= 64) {
                 process(64);
                 // the candidates beyond the first 64 (fewer than 32) move to the front of the list
@@ -392,12 +344,6 @@ __global__ void __launch_bounds__(32 * kRealWarps, SE1P_REAL_MINB) k_real(Geo g,
                 __syncwarp();
                 ncand = rest;
             }
-#else
-            if (ncand >= 64) {
-                process(ncand);
-                ncand = 0;
-            }
-#endif
         }
     }
     if (ncand > 0) process(ncand);

@@ -26,7 +26,7 @@ template <typename T>
 __global__ void k_zfwd(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restrict__ tw, int xb, FastDiv fxb,
                        const T *__restrict__ grid, Cx<T> *__restrict__ zspec, double *__restrict__ slab0)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
     Cx<T> *b = a + (size_t)M3 * xb;
     const int nxc = (Mt + xb - 1) / xb;
@@ -184,7 +184,7 @@ __global__ void k_xfwd(int Mt, int ns, int kfirst, int nrows, FftDesc d, const T
                        FastDiv frb, FastDiv fns, FastDiv fMt, const Cx<T> *__restrict__ zspec,
                        const double *__restrict__ slab0, Cx<T> *__restrict__ rows)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
     Cx<T> *b = a + (size_t)rb * ns;
     const int r0 = blockIdx.x * rb;
@@ -214,7 +214,7 @@ __global__ void k_yscale(int Mt, int ns, int kfirst, int count, FftDesc d, const
                          FastDiv fxb, Cx<T> *__restrict__ rows, const double *__restrict__ sym0,
                          const T *__restrict__ symc)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
     Cx<T> *b = a + (size_t)ns * xb;
     const int nkc = (ns + xb - 1) / xb;
@@ -250,7 +250,7 @@ __global__ void k_xinv(int Mt, int ns, int kfirst, int nrows, FftDesc d, const T
                        FastDiv frb, FastDiv fns, FastDiv fMt, const Cx<T> *__restrict__ rows,
                        Cx<T> *__restrict__ zspec, double *__restrict__ slab0)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
     Cx<T> *b = a + (size_t)rb * ns;
     const int r0 = blockIdx.x * rb;
@@ -275,7 +275,7 @@ template <typename T>
 __global__ void k_zinv(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restrict__ tw, int xb, FastDiv fxb,
                        const Cx<T> *__restrict__ zspec, const double *__restrict__ slab0, T *__restrict__ grid)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
     Cx<T> *b = a + (size_t)M3 * xb;
     const int nxc = (Mt + xb - 1) / xb;
@@ -310,7 +310,7 @@ __global__ void k_zinv_pair(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__re
                             const Cx<T> *__restrict__ zspec, const double *__restrict__ slab0, T *__restrict__ grid)
 {
     using V2 = typename Pair2<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
     Cx<T> *b = a + (size_t)M3 * xp;
     const int npair = Mt / 2, nxc = (npair + xp - 1) / xp;

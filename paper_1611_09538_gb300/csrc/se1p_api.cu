@@ -183,13 +183,12 @@ template <typename T> se1p_status alloc_particles(se1p_plan *p, Alloc &A)
 {
     const int nm = p->n_max > 0 ? p->n_max : 1;
     const Geo &g = p->geo;
-    p->b.grid = A.dev(sizeof(T) * (size_t)p->M3 * p->Mt * p->Mt);
-    p->b.gridf = p->per3 ? A.dev(sizeof(T) * (size_t)p->M3 * p->Mf * p->Mf) : p->b.grid;
+    p->b.grid = A.dev(sizeof(T) * grid_points(p->M3, p->Mt));
+    p->b.gridf = p->per3 ? A.dev(sizeof(T) * grid_points(p->M3, p->Mf)) : p->b.grid;
     p->b.zspec = A.dev(csize<T>() * (size_t)p->K3 * p->Mf * p->Mf);
     p->b.slab0_in = (double *)A.dev(sizeof(double) * (size_t)p->Mf * p->Mf);
     p->b.slab0_out = (double *)A.dev(sizeof(double) * (size_t)p->Mf * p->Mf);
     p->b.sym0 = (double *)A.dev(sizeof(double) * (size_t)p->n0 * p->n0);
-    p->b.dgrid = (double *)A.dev(sizeof(double) * (size_t)p->M3 * p->Mt * p->Mt);
     p->b.xyzq = (double *)A.dev(sizeof(double) * 4 * (size_t)nm);
     p->b.bin_key = (int *)A.dev(sizeof(int) * (size_t)nm);
     p->b.cell_key = (int *)A.dev(sizeof(int) * (size_t)nm);
@@ -215,6 +214,9 @@ template <typename T> se1p_status alloc_particles(se1p_plan *p, Alloc &A)
     p->b.hen = (double *)A.dev(sizeof(double));
     if (!A.ok) return SE1P_ERR_ALLOC;
     cudaMemset(p->b.status, 0, sizeof(int));
+    // the x padding of the last block of each grid row stays zero (kernels write only x < Mt)
+    cudaMemset(p->b.grid, 0, sizeof(T) * grid_points(p->M3, p->Mt));
+    if (p->per3) cudaMemset(p->b.gridf, 0, sizeof(T) * grid_points(p->M3, p->Mf));
     return SE1P_OK;
 }
 

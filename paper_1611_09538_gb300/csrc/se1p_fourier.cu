@@ -33,7 +33,7 @@ __global__ void k_zfwd(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restric
     const int y = blockIdx.x / nxc, x0 = (blockIdx.x % nxc) * xb;
     for (int e = threadIdx.x; e < M3 * xb; e += blockDim.x) {
         const int z = fdiv(e, fxb), p = e - z * xb, x = x0 + p;
-        const T v = x < Mt ? grid[((size_t)z * Mt + y) * Mt + x] : (T)0;
+        const T v = x < Mt ? grid[gidx(z, y, x, Mt, gnxb(Mt))] : (T)0;
         a[e] = cx<T>(v, (T)0);
     }
     __syncthreads();
@@ -83,8 +83,8 @@ template <> struct Pair2<float> { using type = float2; };
 template <> struct Pair2<double> { using type = double2; };
 
 // With a tensor map (tma != 0) the CTA's M3 x 2 xp real values arrive by bulk tensor copies (boxes of
-// 2 xp x 1 x zbox values of the [z][y][x] grid, x beyond the row filled with zeros) that land in
-// shared memory exactly as the complex pencils: value (z, x = 2 (j0 + pp) + r) at a[z xp + pp], part r.
+// the x-blocked grid, blocks beyond the row filled with zeros, padding points holding zeros) that land
+// in shared memory exactly as the complex pencils: value (z, x = 2 (j0 + pp) + r) at a[z xp + pp], part r.
 // The wait on them is bounded (spin_limit polls); a CTA that gives up records FLAG_TIMEOUT in *status,
 // waits for its copies to land (bounded as well) and returns without writing results.
 template <typename T>
@@ -105,7 +105,9 @@ __global__ void k_zfwd_pair(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__re
         if (threadIdx.x == 0) {
             mbar_init(bar_a, 1);
             mbar_expect_tx(bar_a, (unsigned)((size_t)M3 * xp * sizeof(Cx<T>)));
-            for (int z0 = 0; z0 < M3; z0 += zbox) tma_load_3d(smem_addr(a + (size_t)z0 * xp), &tm, 2 * j0, y, z0, bar_a);
+            const int x0 = 2 * j0;  // first real pencil: block x0 / 8, offset x0 % 8 inside it
+            for (int z0 = 0; z0 < M3; z0 += zbox)
+                tma_load_4d(smem_addr(a + (size_t)z0 * xp), &tm, x0 & (kXB - 1), y, x0 / kXB, z0, bar_a);
         }
         __syncthreads();  // the barrier is initialised before anyone polls it
         const bool late = !mbar_wait(bar_a, 0, spin_limit);
@@ -120,7 +122,7 @@ __global__ void k_zfwd_pair(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__re
             const int z = fdiv(e, fxp), pp = e - z * xp, j = j0 + pp;
             Cx<T> v = cx<T>((T)0, (T)0);
             if (j < npair) {
-                const V2 h = *reinterpret_cast<const V2 *>(grid + ((size_t)z * Mt + y) * Mt + 2 * j);
+                const V2 h = *reinterpret_cast<const V2 *>(grid + gidx(z, y, 2 * j, Mt, gnxb(Mt)));  // a pair never straddles a block
                 v = cx<T>(h.x, h.y);
             }
             a[e] = v;
@@ -299,7 +301,7 @@ __global__ void k_zinv(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restric
     Cx<T> *res = fft_smem<T>(a, b, d, xb, fxb, 1, xb, tw, +1);
     for (int e = threadIdx.x; e < M3 * xb; e += blockDim.x) {
         const int z = fdiv(e, fxb), p = e - z * xb, x = x0 + p;
-        if (x < Mt) grid[((size_t)z * Mt + y) * Mt + x] = res[e].re;
+        if (x < Mt) grid[gidx(z, y, x, Mt, gnxb(Mt))] = res[e].re;
     }
 }
 
@@ -344,7 +346,7 @@ __global__ void k_zinv_pair(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__re
             V2 o;
             o.x = res[e].re;
             o.y = res[e].im;
-            *reinterpret_cast<V2 *>(grid + ((size_t)z * Mt + y) * Mt + 2 * j) = o;
+            *reinterpret_cast<V2 *>(grid + gidx(z, y, 2 * j, Mt, gnxb(Mt))) = o;
         }
     }
 }
@@ -446,15 +448,18 @@ template <typename K> cudaError_t allow_max_dynamic_smem(K kernel, int maxsm)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm - (int)fa.sharedSizeBytes);
 }
 
-// Tensor map of the z forward pass: the [z][y][x] grid of T (x fastest), boxes of 2 xb x 1 x zbox values.
-// Used when the pencil pairs' box and the row stride are multiples of 16 bytes (the tensor-copy
-// alignment rules: every copied x offset 2 j0 is then a multiple of 16 bytes too) and zbox, the largest
-// divisor of M3 up to 256 (the box limit per dimension), gives whole boxes.
+// Tensor map of the z forward pass over the x-blocked grid, a 4-D tensor [z][x / 8][y][x % 8] of T:
+// boxes of min(2 xb, 8) x 1 x max(1, 2 xb / 8) x zbox values land in shared memory as [z][2 xb], the
+// CTA's pencil pairs.  Used when the box's inner extent is a multiple of 16 bytes (every copied x
+// offset within a block, 2 j0 mod 8, is then a multiple of 16 bytes too), 2 xb divides or is a multiple
+// of the block, and zbox, the largest divisor of M3 up to 256 (the box limit per dimension), gives whole
+// boxes.
 template <typename T> void make_zfwd_tensor_map(se1p_plan *p)
 {
     p->tma_zfwd = false;
-    const int Mt = p->Mf, M3 = p->M3, xp = p->xb_z;
-    if (!p->zpair || (Mt * sizeof(T)) % 16 != 0 || (2 * xp * sizeof(T)) % 16 != 0 || 2 * xp > 256) return;
+    const int Mt = p->Mf, M3 = p->M3, xp = p->xb_z, nxb = gnxb(Mt);
+    const int bx = 2 * xp < kXB ? 2 * xp : kXB, bxb = 2 * xp < kXB ? 1 : 2 * xp / kXB;
+    if (!p->zpair || (bx * sizeof(T)) % 16 != 0 || (2 * xp) % bx != 0 || bxb > 256) return;
     int zbox = 1;
     for (int v = 1; v <= 256 && v <= M3; ++v)
         if (M3 % v == 0) zbox = v;
@@ -469,12 +474,13 @@ template <typename T> void make_zfwd_tensor_map(se1p_plan *p)
     using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-    const cuuint64_t dims[3] = {(cuuint64_t)Mt, (cuuint64_t)Mt, (cuuint64_t)M3};
-    const cuuint64_t strides[2] = {(cuuint64_t)Mt * sizeof(T), (cuuint64_t)Mt * Mt * sizeof(T)};
-    const cuuint32_t box[3] = {(cuuint32_t)(2 * xp), 1u, (cuuint32_t)zbox};
-    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    const cuuint64_t dims[4] = {(cuuint64_t)kXB, (cuuint64_t)Mt, (cuuint64_t)nxb, (cuuint64_t)M3};
+    const cuuint64_t strides[3] = {(cuuint64_t)kXB * sizeof(T), (cuuint64_t)Mt * kXB * sizeof(T),
+                                   (cuuint64_t)nxb * Mt * kXB * sizeof(T)};
+    const cuuint32_t box[4] = {(cuuint32_t)bx, 1u, (cuuint32_t)bxb, (cuuint32_t)zbox};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
     const CUresult r = reinterpret_cast<Encode>(fn)(
-        &p->tm_zfwd, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, p->b.gridf,
+        &p->tm_zfwd, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, p->b.gridf,
         dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return;

@@ -168,12 +168,12 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase, long lon
     }
     return false;
 }
-// 3-D tiled copy global -> shared of the box at (x, y, z) of tensor map `tm`, completing on `bar`
-__device__ __forceinline__ void tma_load_3d(unsigned dst, const void *tm, int x, int y, int z, unsigned bar)
+// 4-D tiled copy global -> shared of the box at (c0, c1, c2, c3) of tensor map `tm`, completing on `bar`
+__device__ __forceinline__ void tma_load_4d(unsigned dst, const void *tm, int c0, int c1, int c2, int c3, unsigned bar)
 {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(tm)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
         : "memory");
 }
 constexpr long long kDrainPolls = 1ll << 24;  // bound of the wait for copies still in flight after a timeout
@@ -445,5 +445,19 @@ struct Geo {
 };
 
 constexpr int kBin = 8;  // spread bin / tile edge in grid points
+
+// Storage of the real grids (the gridding output, the transformed grid, and the periodic grid of
+// triply periodic plans): x-blocks of kXB points, [z][x / kXB][y][x % kXB], with n x n points per
+// z plane stored as gnxb(n) blocks of n rows.  The rows of one block are kXB values apart, so the
+// kXB x-points of consecutive y rows are contiguous: a warp reading a particle's support touches
+// whole 128-byte lines (four FP32 rows per line) instead of one or two lines per row.  x points
+// from n up to the end of the last block are padding and hold zeros.
+constexpr int kXB = 8;
+__host__ __device__ __forceinline__ int gnxb(int n) { return (n + kXB - 1) / kXB; }
+__host__ __device__ __forceinline__ size_t gidx(int z, int y, int x, int n, int nxb)
+{
+    return (((size_t)z * nxb + (x >> 3)) * n + y) * kXB + (x & (kXB - 1));
+}
+__host__ __device__ __forceinline__ size_t grid_points(int M3, int n) { return (size_t)M3 * gnxb(n) * n * kXB; }
 
 }  // namespace se1p

@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int *__r
         for (int r = 0; r < 4; ++r) {
             const int z = z0 + tz + (r >> 1), y = y0 + ty + (r & 1);
             if (z < M3 && y < g.Mt) {
-                T *dst = grid + ((size_t)z * g.Mt + y) * g.Mt + x0;
+                T *dst = grid + gidx(z, y, x0, g.Mt, gnxb(g.Mt));  // x0 = 8 k: one whole block row
 #pragma unroll
                 for (int c = 0; c < kBin; ++c) {
                     T v = acc[r][c];
@@ -563,7 +563,7 @@ __global__ void __launch_bounds__(256) k_gather(Geo g, int n, const PartRec<T> *
             for (int k = 0; k < P; ++k) {
                 int zk = r.i0[2] + k;
                 if (zk >= g.M3) zk -= g.M3;
-                const T *row = grid + ((size_t)zk * g.Mt + r.i0[1]) * g.Mt + r.i0[0] + lane;
+                const int xl = r.i0[0] + lane, nxb = gnxb(g.Mt);
                 T a = 0, b = 0;
 #pragma unroll(PC > 0 ? (PC + 1) / 2 : 1)
                 for (int j = 0; j < P; j += 2) {
@@ -580,8 +580,8 @@ __global__ void __launch_bounds__(256) k_gather(Geo g, int n, const PartRec<T> *
                         wy1 = sy[wib][j + 1][0];
                         wd1 = sy[wib][j + 1][1];
                     }
-                    const T v0 = __ldg(row + (size_t)j * g.Mt);
-                    const T v1 = j + 1 < P ? __ldg(row + (size_t)(j + 1) * g.Mt) : (T)0;
+                    const T v0 = __ldg(grid + gidx(zk, r.i0[1] + j, xl, g.Mt, nxb));
+                    const T v1 = j + 1 < P ? __ldg(grid + gidx(zk, r.i0[1] + j + 1, xl, g.Mt, nxb)) : (T)0;
                     a += wy0 * v0;
                     b += wd0 * v0;
                     a += wy1 * v1;
@@ -616,38 +616,43 @@ template <> __device__ __forceinline__ double2 make_zero<double2>() { return mak
 __device__ __forceinline__ float dotv(const float *w, float4 v) { return w[0] * v.x + w[1] * v.y + w[2] * v.z + w[3] * v.w; }
 __device__ __forceinline__ double dotv(const double *w, double2 v) { return w[0] * v.x + w[1] * v.y; }
 
-// Vectorised gathering for Mt a multiple of V = 16 / sizeof(T) (every grid row then
-// starts 16-byte aligned).  The x window [i0, i0+P) is covered from the aligned
-// start i0 & ~(V-1) by NQ = ceil((P + V - 1) / V) vectors; a warp instruction
-// loads RPR = 32 / NQ rows at once (lane = row-in-group x vector), so one request
-// brings 4 rows (FP32, P = 24) instead of one.  Each lane holds the x window
-// values of its V points (zero outside the support) and accumulates, per row,
-// sum wx H and sum wx dx H, weighted by the row's y values (wy, wy dy).
+// Vectorised gathering on the x-blocked grid.  A particle's x support [i0, i0 + P) lies in NB blocks
+// of kXB points starting at block i0 / kXB; a warp request covers two blocks x RG rows x the block's
+// VPB 16-byte vectors (32 lanes: lane = (block of the pair, row, vector)), i.e. two 256-byte runs of
+// consecutive rows, whole 128-byte lines.  Each lane holds the x window values of its V points (zero
+// outside the support) for each pair of blocks and accumulates, per row, sum wx H and sum wx dx H,
+// weighted by the row's y values (wy, wy dy); the z rows are weighted at the end of each z level.
+// FP32 is compiled for four CTAs per SM (64 registers): with the loads of four z levels in flight the
+// kernel is latency-bound, and 32 resident warps beat 24 (C2 alone 0.356 against 0.407 ms).
 template <typename T, int PC>
-__global__ void __launch_bounds__(256) k_gather_vec(Geo g, int n, const PartRec<T> *__restrict__ parts,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_gather_vec(Geo g, int n, const PartRec<T> *__restrict__ parts,
                                                     const T *__restrict__ wts, const T *__restrict__ grid,
                                                     double *__restrict__ phi, double *__restrict__ frc,
                                                     int flags, GatherScale sc)
 {
-    constexpr int V = 16 / sizeof(T);
-    constexpr int NQ = (PC + V - 1 + V - 1) / V;
-    constexpr int RPR = 32 / NQ;                       // rows per warp request
-    constexpr int NJ = (PC + RPR - 1) / RPR * RPR;     // y rows padded to a multiple of RPR
+    constexpr int V = 16 / sizeof(T);                    // values per 16-byte vector
+    constexpr int VPB = kXB / V;                         // vectors per block row
+    constexpr int RG = 32 / (2 * VPB);                   // rows per request
+    constexpr int NB = (PC + kXB - 1 + kXB - 1) / kXB;   // blocks a support can touch
+    constexpr int NBP = (NB + 1) / 2;                    // block pairs
+    constexpr int NRG = (PC + RG - 1) / RG;              // row groups
+    constexpr int NJ = NRG * RG;                         // y rows padded to a multiple of RG
     using VecT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
     __shared__ T sy[8][2][NJ];
     __shared__ T sz[8][2][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int rr = lane / NQ, qv = lane - rr * NQ;  // row within the request, vector index
-    const bool active = rr < RPR;
+    const int bi = lane / (RG * VPB), rem = lane - bi * (RG * VPB);
+    const int r = rem / VPB, qv = rem - r * VPB;  // row within the request, vector within the block row
+    const int nxb = gnxb(g.Mt);
     const int warps_total = gridDim.x * (blockDim.x >> 5);
     for (int pi = blockIdx.x * (blockDim.x >> 5) + wib; pi < n; pi += warps_total) {
-        const PartRec<T> r = parts[pi];
+        const PartRec<T> pr = parts[pi];
         const T *w = wts + (size_t)pi * 3 * PC;
         for (int j = lane; j < NJ; j += 32) {
             T wy = 0, wyd = 0;
             if (j < PC) {
                 wy = w[PC + j];
-                wyd = wy * (r.g[1] - (T)(j - g.c));
+                wyd = wy * (pr.g[1] - (T)(j - g.c));
             }
             sy[wib][0][j] = wy;
             sy[wib][1][j] = wyd;
@@ -655,58 +660,66 @@ __global__ void __launch_bounds__(256) k_gather_vec(Geo g, int n, const PartRec<
         if (lane < PC) {
             const T wz = w[2 * PC + lane];
             sz[wib][0][lane] = wz;
-            sz[wib][1][lane] = wz * (r.g[2] - (T)(lane - g.c));
+            sz[wib][1][lane] = wz * (pr.g[2] - (T)(lane - g.c));
         }
-        // this lane's V x points: window index rel = base + V qv + e - i0
-        const int base = r.i0[0] & ~(V - 1);
-        T wx[V], wxd[V];
+        // this lane's V x points in each block pair: x = (xb0 + 2 bp + bi) kXB + V qv + e
+        const int xb0 = pr.i0[0] / kXB;
+        T wx[NBP][V], wxd[NBP][V];
+        bool ld[NBP];
+        int loff[NBP];  // offset of this lane's first vector inside a z plane, row i0y + r
 #pragma unroll
-        for (int e = 0; e < V; ++e) {
-            const int rel = base + V * qv + e - r.i0[0];
-            const bool in = active && rel >= 0 && rel < PC;
-            wx[e] = in ? w[rel] : (T)0;
-            wxd[e] = in ? wx[e] * (r.g[0] - (T)(rel - g.c)) : (T)0;
+        for (int bp = 0; bp < NBP; ++bp) {
+            const int blk = xb0 + 2 * bp + bi;
+            // a block is read when it exists and holds at least one support point
+            ld[bp] = blk < nxb && blk * kXB < pr.i0[0] + PC;
+            loff[bp] = (blk * g.Mt + pr.i0[1] + r) * kXB + V * qv;
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const int rel = blk * kXB + V * qv + e - pr.i0[0];
+                const bool in = rel >= 0 && rel < PC;
+                wx[bp][e] = in ? w[rel] : (T)0;
+                wxd[bp][e] = in ? wx[bp][e] * (pr.g[0] - (T)(rel - g.c)) : (T)0;
+            }
         }
-        // only vectors holding at least one window point are read: such a vector starts at a
-        // multiple of V below i0 + P <= Mt and so ends inside the row (Mt % V == 0)
-        const bool ld = active && (base + V * qv < r.i0[0] + PC);
         __syncwarp();
         T aphi = 0, afx = 0, afy = 0, afz = 0;
-        if (ld) {
-#pragma unroll 4  // several z rows' loads in flight (measured: 0.49 -> 0.42 ms at C2)
-            for (int k = 0; k < PC; ++k) {
-                int zk = r.i0[2] + k;
-                if (zk >= g.M3) zk -= g.M3;
-                const T *rowbase = grid + ((size_t)zk * g.Mt + r.i0[1]) * g.Mt + base + V * qv;
-                T a = 0, b = 0, c = 0;
+        const size_t plane = (size_t)nxb * g.Mt * kXB;
+#pragma unroll 4  // several z levels' loads in flight
+        for (int k = 0; k < PC; ++k) {
+            int zk = pr.i0[2] + k;
+            if (zk >= g.M3) zk -= g.M3;
+            const T *gk = grid + (size_t)zk * plane;
+            T a = 0, b = 0, c = 0;
 #pragma unroll
-                for (int j0 = 0; j0 < NJ; j0 += RPR) {
-                    const int j = j0 + rr;
-                    const T wy = sy[wib][0][j], wyd = sy[wib][1][j];
+            for (int rg = 0; rg < NRG; ++rg) {
+                const int j = rg * RG + r;
+                const T wy = sy[wib][0][j], wyd = sy[wib][1][j];
+#pragma unroll
+                for (int bp = 0; bp < NBP; ++bp) {
                     VecT v = make_zero<VecT>();
-                    if (j < PC) v = *reinterpret_cast<const VecT *>(rowbase + (size_t)j * g.Mt);
-                    const T s1 = dotv(wx, v), s2 = dotv(wxd, v);
+                    if (ld[bp] && j < PC) v = *reinterpret_cast<const VecT *>(gk + loff[bp] + rg * RG * kXB);
+                    const T s1 = dotv(wx[bp], v), s2 = dotv(wxd[bp], v);
                     a += wy * s1;
                     b += wy * s2;
                     c += wyd * s1;
                 }
-                const T wz = sz[wib][0][k], wzd = sz[wib][1][k];
-                aphi += wz * a;
-                afx += wz * b;
-                afy += wz * c;
-                afz += wzd * a;
             }
+            const T wz = sz[wib][0][k], wzd = sz[wib][1][k];
+            aphi += wz * a;
+            afx += wz * b;
+            afy += wz * c;
+            afz += wzd * a;
         }
         const T vphi = warp_sum(aphi), vfx = warp_sum(afx), vfy = warp_sum(afy), vfz = warp_sum(afz);
         if (lane == 0) {
-            const double qd = (double)r.q;
+            const double qd = (double)pr.q;
             double ph = sc.phi * (double)vphi;
             if (flags & 1) ph += -2.0 * g.xi / sqrt(kPi) * qd;
-            phi[r.orig] = ph;
+            phi[pr.orig] = ph;
             const double qf = (flags & 2) ? 1.0 : qd;
-            frc[3 * r.orig + 0] = qf * sc.fxy * (double)vfx;
-            frc[3 * r.orig + 1] = qf * sc.fxy * (double)vfy;
-            frc[3 * r.orig + 2] = qf * sc.fz * (double)vfz;
+            frc[3 * pr.orig + 0] = qf * sc.fxy * (double)vfx;
+            frc[3 * pr.orig + 1] = qf * sc.fxy * (double)vfy;
+            frc[3 * pr.orig + 2] = qf * sc.fz * (double)vfz;
         }
         __syncwarp();
     }
@@ -780,11 +793,28 @@ __global__ void k_vjp_combine(int n, const double *__restrict__ q, const double 
     }
 }
 
-template <typename TS, typename TD>
-__global__ void k_convert(size_t n, const TS *__restrict__ src, TD *__restrict__ dst, double scale)
+// Conversions between a plan's grid (T, x-blocks) and the [z][y][x] FP64 grids of the single-step
+// entry points; i runs over the M3 x Mt x Mt points in [z][y][x] order.
+template <typename T>
+__global__ void k_grid_to_user(int M3, int Mt, const T *__restrict__ src, double *__restrict__ dst, double scale)
 {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        dst[i] = (TD)((double)src[i] * scale);
+    const size_t n = (size_t)M3 * Mt * Mt;
+    const int nxb = gnxb(Mt);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % Mt), y = (int)((i / Mt) % Mt), z = (int)(i / ((size_t)Mt * Mt));
+        dst[i] = (double)src[gidx(z, y, x, Mt, nxb)] * scale;
+    }
+}
+
+template <typename T>
+__global__ void k_grid_from_user(int M3, int Mt, const double *__restrict__ src, T *__restrict__ dst)
+{
+    const size_t n = (size_t)M3 * Mt * Mt;
+    const int nxb = gnxb(Mt);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % Mt), y = (int)((i / Mt) % Mt), z = (int)(i / ((size_t)Mt * Mt));
+        dst[gidx(z, y, x, Mt, nxb)] = (T)src[i];
+    }
 }
 
 // Triply periodic plans grid on the extended grid (Mt = M + P, origin -P h/2) and transform the
@@ -795,13 +825,13 @@ template <typename T>
 __global__ void k_fold(int M3, int Mt, int Mf, int sh, const T *__restrict__ ext, T *__restrict__ per)
 {
     const size_t total = (size_t)M3 * Mf * Mf;
+    const int nxbt = gnxb(Mt), nxbf = gnxb(Mf);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int jx = (int)(i % Mf), jy = (int)((i / Mf) % Mf), z = (int)(i / ((size_t)Mf * Mf));
-        const T *plane = ext + (size_t)z * Mt * Mt;
         T acc = (T)0;
         for (int iy = (jy + sh) % Mf; iy < Mt; iy += Mf)
-            for (int ix = (jx + sh) % Mf; ix < Mt; ix += Mf) acc += plane[(size_t)iy * Mt + ix];
-        per[i] = acc;
+            for (int ix = (jx + sh) % Mf; ix < Mt; ix += Mf) acc += ext[gidx(z, iy, ix, Mt, nxbt)];
+        per[gidx(z, jy, jx, Mf, nxbf)] = acc;
     }
 }
 
@@ -809,10 +839,11 @@ template <typename T>
 __global__ void k_unfold(int M3, int Mt, int Mf, int sh, const T *__restrict__ per, T *__restrict__ ext)
 {
     const size_t total = (size_t)M3 * Mt * Mt;
+    const int nxbt = gnxb(Mt), nxbf = gnxb(Mf);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int ix = (int)(i % Mt), iy = (int)((i / Mt) % Mt), z = (int)(i / ((size_t)Mt * Mt));
         const int jx = (ix - sh + Mf) % Mf, jy = (iy - sh + Mf) % Mf;  // sh = P/2 <= Mf
-        ext[i] = per[((size_t)z * Mf + jy) * Mf + jx];
+        ext[gidx(z, iy, ix, Mt, nxbt)] = per[gidx(z, jy, jx, Mf, nxbf)];
     }
 }
 
@@ -873,7 +904,7 @@ template <typename T> void launch_spread(se1p_plan *p, cudaStream_t s)
     const Geo &g = p->geo;
     const int nt = (g.Mt + kBin - 1) / kBin;
     const int ntz = (g.M3 + kBin - 1) / kBin;
-    cudaMemsetAsync(p->b.grid, 0, sizeof(T) * (size_t)g.M3 * g.Mt * g.Mt, s);
+    cudaMemsetAsync(p->b.grid, 0, sizeof(T) * grid_points(g.M3, g.Mt), s);
     k_spread<T><<<nt * nt * ntz * kSpreadSplit, kSpreadThreads, 0, s>>>(g, p->b.starts, (const PartRec<T> *)p->b.parts,
                                               (const T *)p->b.wts, (T *)p->b.grid);
 }
@@ -899,8 +930,7 @@ void launch_gather(se1p_plan *p, int n, const void *grid, double *phi, double *f
     const T *w = (const T *)p->b.wts;
     const T *gr = (const T *)grid;
     const int nt = 32 * warps_per_block;
-    constexpr int V = 16 / sizeof(T);
-    const bool vec = g.Mt % V == 0;
+    const bool vec = true;  // the x-blocked grid keeps every block row 16-byte aligned
     if (vec && g.P == 24) k_gather_vec<T, 24><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
     else if (vec && g.P == 16) k_gather_vec<T, 16><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
     else if (vec && g.P == 12) k_gather_vec<T, 12><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
@@ -928,13 +958,13 @@ template <typename T>
 void launch_grid_to_double(se1p_plan *p, const void *src, double *dst, double scale, cudaStream_t s)
 {
     const size_t n = (size_t)p->M3 * p->Mt * p->Mt;
-    k_convert<T, double><<<blocks_for(n, 256, 4096), 256, 0, s>>>(n, (const T *)src, dst, scale);
+    k_grid_to_user<T><<<blocks_for(n, 256, 4096), 256, 0, s>>>(p->M3, p->Mt, (const T *)src, dst, scale);
 }
 
 template <typename T> void launch_grid_from_double(se1p_plan *p, const double *src, void *dst, cudaStream_t s)
 {
     const size_t n = (size_t)p->M3 * p->Mt * p->Mt;
-    k_convert<double, T><<<blocks_for(n, 256, 4096), 256, 0, s>>>(n, src, (T *)dst, 1.0);
+    k_grid_from_user<T><<<blocks_for(n, 256, 4096), 256, 0, s>>>(p->M3, p->Mt, src, (T *)dst);
 }
 
 template <typename T> int configure_particle_kernels() { return 0; }

@@ -24,8 +24,8 @@ struct SlabClass {
 };
 
 struct Buffers {
-    void *grid = nullptr;        // T [M3][Mt][Mt]
-    void *gridf = nullptr;       // T [M3][Mf][Mf] periodic grid of the FFTs (triply periodic plans; else = grid)
+    void *grid = nullptr;        // T, M3 x Mt x Mt points in x-blocks (gidx)
+    void *gridf = nullptr;       // T, M3 x Mf x Mf periodic grid of the FFTs (triply periodic plans; else = grid)
     void *zspec = nullptr;       // Cx<T> [K3][Mt][Mt]  (k3 = 0 entry unused)
     double *slab0_in = nullptr;  // k3 = 0 coefficient of H, [Mt][Mt]
     double *slab0_out = nullptr; // k3 = 0 coefficient of Ht, [Mt][Mt]
@@ -49,7 +49,6 @@ struct Buffers {
     int *status = nullptr;
     double *hx = nullptr, *hq = nullptr, *hphi = nullptr, *hfrc = nullptr, *hen = nullptr;  // host staging
     int *hstatus = nullptr;  // page-locked copy of the status word (host entry point)
-    double *dgrid = nullptr;     // FP64 grid for stage entry points [M3][Mt][Mt]
 };
 
 constexpr int kEnergyBlocks = 256;

@@ -267,7 +267,7 @@ se1p_plan *se1p_batch_plan(se1p_batch *batch, int i);
  *
  * It takes the parameters directly (no plan: plan creation allocates) and uses
  * params->L, xi, rc (> 0, <= L3) and precision.  All scratch lives in one
- * file-scope __device__ array of about 1.7 MB that every GPU which loads the
+ * file-scope __device__ array of about 2.2 MB that every GPU which loads the
  * library holds until the process exits; nothing is allocated or freed (no
  * cudaMalloc, cudaFree or allocating library routine).
  *   - n <= 16384 particles (larger n returns SE1P_ERR_CAPACITY); the cell list

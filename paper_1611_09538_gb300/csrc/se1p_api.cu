@@ -203,6 +203,7 @@ template <typename T> se1p_status alloc_particles(se1p_plan *p, Alloc &A)
     p->b.frc_int = (double *)A.dev(sizeof(double) * 3 * (size_t)nm);
     p->b.phi2 = (double *)A.dev(sizeof(double) * (size_t)nm);
     p->b.frc2 = (double *)A.dev(sizeof(double) * 3 * (size_t)nm);
+    if (sizeof(T) == sizeof(double)) p->b.rsum = (double *)A.dev(sizeof(double) * 4 * (size_t)nm);
     p->b.sums = (double *)A.dev(sizeof(double) * 2);
     p->b.epart = (double *)A.dev(sizeof(double) * kEnergyBlocks);
     p->b.status = (int *)A.dev(sizeof(int));

@@ -36,6 +36,7 @@ constexpr int kNaMaxDevices = 64;
 //   counts  int     [kNaMaxCells]
 //   starts  int     [kNaMaxCells + 2]        starts[0] is padding, cell starts from starts[1]
 //   cursor  int     [kNaMaxCells]
+//   rsum    double  [4][kNaMaxParticles]     real-space sums in cell order
 constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 constexpr size_t kOffXyzq = 0;
 constexpr size_t kOffKey = kOffXyzq + align256(sizeof(double) * 4 * kNaMaxParticles);
@@ -43,7 +44,8 @@ constexpr size_t kOffCells = kOffKey + align256(sizeof(int) * kNaMaxParticles);
 constexpr size_t kOffCounts = kOffCells + align256(sizeof(CellRec<double>) * kNaMaxParticles);
 constexpr size_t kOffStarts = kOffCounts + align256(sizeof(int) * kNaMaxCells);
 constexpr size_t kOffCursor = kOffStarts + align256(sizeof(int) * (kNaMaxCells + 2));
-constexpr size_t kScratchBytes = kOffCursor + align256(sizeof(int) * kNaMaxCells);
+constexpr size_t kOffRsum = kOffCursor + align256(sizeof(int) * kNaMaxCells);
+constexpr size_t kScratchBytes = kOffRsum + align256(sizeof(double) * 4 * kNaMaxParticles);
 
 static __device__ __align__(256) unsigned char g_na_scratch[kScratchBytes];
 
@@ -165,6 +167,7 @@ se1p_status na_run(const se1p_params &P, const Geo &g, unsigned char *scr, int n
     int *counts = reinterpret_cast<int *>(scr + kOffCounts);
     int *starts = reinterpret_cast<int *>(scr + kOffStarts);
     int *cursor = reinterpret_cast<int *>(scr + kOffCursor);
+    double *rsum = reinterpret_cast<double *>(scr + kOffRsum);
     // counts must start at zero on every call (the array keeps the previous call's values)
     if (cudaMemsetAsync(counts, 0, sizeof(int) * g.ncells, s) != cudaSuccess) return SE1P_ERR_CUDA;
     const int bs = 256, nb = (n + bs - 1) / bs;
@@ -178,6 +181,7 @@ se1p_status na_run(const se1p_params &P, const Geo &g, unsigned char *scr, int n
     view.geo = g;
     view.b.starts = starts;  // cell starts begin at starts + nbins + 1 = starts + 1
     view.b.cells = cells;
+    view.b.rsum = rsum;
     launch_real_space<T>(&view, n, key, phi, force, 0, s);
     return cudaGetLastError() == cudaSuccess ? SE1P_OK : SE1P_ERR_CUDA;
 }

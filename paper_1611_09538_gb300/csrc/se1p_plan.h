@@ -44,6 +44,7 @@ struct Buffers {
     double *frc_int = nullptr;   // [n_max][3]
     double *phi2 = nullptr;      // [n_max]     second evaluation of the adjoint
     double *frc2 = nullptr;      // [n_max][3]
+    double *rsum = nullptr;      // [4][n_max] FP64 real-space sums (phi, field) in cell order
     double *sums = nullptr;      // [2] sum q, sum |q|
     double *epart = nullptr;     // [kEnergyBlocks]
     int *status = nullptr;

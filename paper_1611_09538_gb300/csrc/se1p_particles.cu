@@ -357,6 +357,10 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(Geo g, int n, const
 // shared loads (its z, y and x window values) for 32 FMAs; the CTA's eight
 // groups take alternate particles and their partial tiles are added at the end.
 // Particles are visited bin by bin (bins of 8 support-start indices per axis).
+// At the end every group's partial tile goes to shared memory (reusing the batch
+// buffers) and all threads sum it, each 4 of the 512 points over the 8 groups
+// (one half-warp summing the others' partial tiles made up a large part of the
+// time of tiles with few particles: N = 10^6 in [1, 1, 8], 3.57 -> 3.21 ms).
 // A batch of 128 records is loaded once into shared memory, then one thread
 // per (particle, axis) gathers the window values at the tile's 8 offsets
 // (zero outside the support, charge folded into z).
@@ -367,16 +371,28 @@ constexpr int kSpreadThreads = 16 * kSpreadGroups;
 // (0.44 against 0.58 ms at C2); alongside the concurrent real space, 1 leaves it more of the SMs
 // and the evaluation is faster (1.599 against 1.610 ms).
 constexpr int kSpreadSplit = 1;
+// CTAs per SM the kernel is compiled for (72 registers in FP32): against the compiler's own choice
+// (68) and six (80), seven gave the fastest evaluations (N = 10^5: 1.461 ms; N = 10^6 in [1, 1, 8]:
+// 11.51 ms; 64 systems: 17.84 ms)
+constexpr int kSpreadMinBlocks = 7;
 
 template <typename T>
-__global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int *__restrict__ bin_start,
+__global__ void __launch_bounds__(kSpreadThreads, kSpreadMinBlocks) k_spread(Geo g, const int *__restrict__ bin_start,
                                                            const PartRec<T> *__restrict__ parts,
                                                            const T *__restrict__ wts, T *__restrict__ grid)
 {
-    __shared__ __align__(16) T sw[kSpreadBatch][3][kBin];
-    __shared__ int soff[kSpreadBatch][3];
-    __shared__ T sq[kSpreadBatch];
-    __shared__ __align__(16) T red[kSpreadGroups - 1][16][4][kBin];
+    // the groups' partial tiles for the final sum: [group][r kBin + c][thread], each group's block
+    // padded by 16 values so that the two groups of a warp store to different banks; it reuses the
+    // batch buffers (window values, offsets, charges)
+    constexpr int kRedStride = 4 * kBin * 16 + 16;
+    constexpr size_t kSwBytes = sizeof(T) * kSpreadBatch * 3 * kBin, kOffBytes = sizeof(int) * kSpreadBatch * 3;
+    constexpr size_t kBatchBytes = kSwBytes + kOffBytes + sizeof(T) * kSpreadBatch;
+    constexpr size_t kRedBytes = sizeof(T) * kSpreadGroups * kRedStride;
+    __shared__ __align__(16) unsigned char sraw[kBatchBytes > kRedBytes ? kBatchBytes : kRedBytes];
+    T(*sw)[3][kBin] = reinterpret_cast<T(*)[3][kBin]>(sraw);
+    int(*soff)[3] = reinterpret_cast<int(*)[3]>(sraw + kSwBytes);
+    T *sq = reinterpret_cast<T *>(sraw + kSwBytes + kOffBytes);
+    T(*red)[kRedStride] = reinterpret_cast<T(*)[kRedStride]>(sraw);
     const int ntx = (g.Mt + kBin - 1) / kBin, nty = ntx;
     const int tile = blockIdx.x / kSpreadSplit, part = blockIdx.x % kSpreadSplit;
     const int txi = tile % ntx, tyi = (tile / ntx) % nty, tzi = tile / (ntx * nty);
@@ -403,6 +419,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int *__r
     int u = 0;
     int zb_iter = 0;
     int zcount = 0;  // z bins seen so far; this CTA takes those with zcount % kSpreadSplit == part
+    bool any = false;  // the tile saw a particle (the same for every thread of the CTA)
     while (true) {
         int bz;
         if (allz) {
@@ -423,6 +440,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int *__r
             const int beg = bin_start[row + bx_lo], end = bin_start[row + bx_hi + 1];
             for (int b0 = beg; b0 < end; b0 += kSpreadBatch) {
                 const int nb = min(kSpreadBatch, end - b0);
+                any = true;
                 __syncthreads();  // previous batch fully consumed
                 for (int b = threadIdx.x; b < nb; b += kSpreadThreads) {
                     const PartRec<T> pr = parts[b0 + b];
@@ -494,29 +512,26 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int *__r
                 acc[r][2 * j + 1] = v.y;
             }
     }
+    if (!any) return;  // nothing to add to the zeroed grid
     __syncthreads();
-    if (grp > 0) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int c = 0; c < kBin; ++c) red[grp - 1][tl][r][c] = acc[r][c];
-    }
+        for (int c = 0; c < kBin; ++c) red[grp][(r * kBin + c) * 16 + tl] = acc[r][c];
     __syncthreads();
-    if (grp == 0) {
+    // every thread sums 4 of the tile's 512 points over the groups (point p = (z 8 + y) 8 + x, held
+    // by thread (z / 2) 4 + y / 2 of each group as its value (z % 2) 2 + y % 2, column x)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int z = z0 + tz + (r >> 1), y = y0 + ty + (r & 1);
-            if (z < M3 && y < g.Mt) {
-                T *dst = grid + gidx(z, y, x0, g.Mt, gnxb(g.Mt));  // x0 = 8 k: one whole block row
+    for (int k = 0; k < 4; ++k) {
+        const int pidx = (int)threadIdx.x + kSpreadThreads * k;
+        const int zz = pidx >> 6, yy = (pidx >> 3) & 7, xx = pidx & 7;
+        const int src = (((zz & 1) * 2 + (yy & 1)) * kBin + xx) * 16 + (zz >> 1) * 4 + (yy >> 1);
+        T v = (T)0;
 #pragma unroll
-                for (int c = 0; c < kBin; ++c) {
-                    T v = acc[r][c];
-#pragma unroll
-                    for (int q = 0; q < kSpreadGroups - 1; ++q) v += red[q][tl][r][c];
-                    if (x0 + c < g.Mt) atomicAdd(dst + c, v);  // the grid is zeroed before the launch
-                }
-            }
-        }
+        for (int q = 0; q < kSpreadGroups; ++q) v += red[q][src];
+        const int z = z0 + zz, y = y0 + yy;
+        // the grid is zeroed before the launch: points outside every support (exact zeros) add nothing
+        if (v != (T)0 && z < M3 && y < g.Mt && x0 + xx < g.Mt) atomicAdd(grid + gidx(z, y, x0 + xx, g.Mt, gnxb(g.Mt)), v);
     }
 }
 

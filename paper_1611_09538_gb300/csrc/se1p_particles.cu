@@ -356,7 +356,11 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(Geo g, int n, const
 // 2(z) x 2(y) x 8(x) points per thread, so each particle costs a thread 4
 // shared loads (its z, y and x window values) for 32 FMAs; the CTA's eight
 // groups take alternate particles and their partial tiles are added at the end.
-// Particles are visited bin by bin (bins of 8 support-start indices per axis).
+// The tile's particles are those of the bins (8 support-start indices per axis)
+// whose supports can reach it: a few (z, y) rows of bins, each one contiguous
+// range of the bin-sorted records; the ranges are loaded together and taken as one
+// list in full batches (batches per row left many partial ones where tiles hold few
+// particles).
 // At the end every group's partial tile goes to shared memory (reusing the batch
 // buffers) and all threads sum it, each 4 of the 512 points over the 8 groups
 // (one half-warp summing the others' partial tiles made up a large part of the
@@ -371,13 +375,16 @@ constexpr int kSpreadThreads = 16 * kSpreadGroups;
 // (0.44 against 0.58 ms at C2); alongside the concurrent real space, 1 leaves it more of the SMs
 // and the evaluation is faster (1.599 against 1.610 ms).
 constexpr int kSpreadSplit = 1;
-// CTAs per SM the kernel is compiled for (72 registers in FP32): against the compiler's own choice
+// CTAs per SM the FP32 kernel is compiled for (72 registers): against the compiler's own choice
 // (68) and six (80), seven gave the fastest evaluations (N = 10^5: 1.461 ms; N = 10^6 in [1, 1, 8]:
 // 11.51 ms; 64 systems: 17.84 ms)
 constexpr int kSpreadMinBlocks = 7;
+// rows of bins per tile: at most 7 z bins (a cyclic range of P + 7 <= 39 starts, or all of a z axis
+// shorter than P + 23) times 6 y bins (P <= 32)
+constexpr int kSpreadMaxRows = 64;
 
 template <typename T>
-__global__ void __launch_bounds__(kSpreadThreads, kSpreadMinBlocks) k_spread(Geo g, const int *__restrict__ bin_start,
+__global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? kSpreadMinBlocks : 1) k_spread(Geo g, const int *__restrict__ bin_start,
                                                            const PartRec<T> *__restrict__ parts,
                                                            const T *__restrict__ wts, T *__restrict__ grid)
 {
@@ -414,90 +421,133 @@ __global__ void __launch_bounds__(kSpreadThreads, kSpreadMinBlocks) k_spread(Geo
     // bins whose start indices can reach the tile
     const int bx_lo = max(x0 - P + 1, 0) / kBin, bx_hi = min(x0 + kBin - 1, g.Mt - P) / kBin;
     const int by_lo = max(y0 - P + 1, 0) / kBin, by_hi = min(y0 + kBin - 1, g.Mt - P) / kBin;
-    const int span = P + kBin - 1;  // cyclic range of z starts [z0-P+1, z0+7]
-    const bool allz = span + 2 * kBin > M3;
-    int u = 0;
-    int zb_iter = 0;
-    int zcount = 0;  // z bins seen so far; this CTA takes those with zcount % kSpreadSplit == part
-    bool any = false;  // the tile saw a particle (the same for every thread of the CTA)
-    while (true) {
-        int bz;
-        if (allz) {
-            if (zb_iter >= g.nbz) break;
-            bz = zb_iter++;
-        } else {
-            if (u >= span) break;
-            int s = z0 - P + 1 + u;
-            if (s < 0) s += M3;
-            if (s >= M3) s -= M3;
-            bz = s / kBin;
-            u += min((bz + 1) * kBin, M3) - s;
+    __shared__ int zbl[8], nzb_s;
+    __shared__ int rbeg[kSpreadMaxRows], rpre[kSpreadMaxRows + 1];
+    __shared__ int sidx[kSpreadBatch];  // record index of each particle of the batch
+    if (threadIdx.x == 0) {
+        // z bins: the cyclic range of starts [z0 - P + 1, z0 + 7], or all of them on a short z axis;
+        // this CTA takes those with (visit count) % kSpreadSplit == part
+        const int span = P + kBin - 1;
+        const bool allz = span + 2 * kBin > M3;
+        int nz = 0, u = 0, zb_iter = 0, zcount = 0;
+        while (true) {
+            int bz;
+            if (allz) {
+                if (zb_iter >= g.nbz) break;
+                bz = zb_iter++;
+            } else {
+                if (u >= span) break;
+                int s = z0 - P + 1 + u;
+                if (s < 0) s += M3;
+                if (s >= M3) s -= M3;
+                bz = s / kBin;
+                u += min((bz + 1) * kBin, M3) - s;
+            }
+            if ((zcount++ % kSpreadSplit) != part) continue;
+            if (nz < 8) zbl[nz++] = bz;
         }
-        if ((zcount++ % kSpreadSplit) != part) continue;
-        if (bx_lo > bx_hi || by_lo > by_hi) continue;
-        for (int by = by_lo; by <= by_hi; ++by) {
-            const int row = (bz * g.nby + by) * g.nbx;
-            const int beg = bin_start[row + bx_lo], end = bin_start[row + bx_hi + 1];
-            for (int b0 = beg; b0 < end; b0 += kSpreadBatch) {
-                const int nb = min(kSpreadBatch, end - b0);
-                any = true;
-                __syncthreads();  // previous batch fully consumed
-                for (int b = threadIdx.x; b < nb; b += kSpreadThreads) {
-                    const PartRec<T> pr = parts[b0 + b];
-                    // support offset of the tile origin per axis; z taken cyclically into [0, M3), so
-                    // that dz + o needs one wrap (a plain difference misses the wrapped part of the
-                    // support when M3 < P + 8)
-                    int dz = z0 - pr.i0[2];
-                    if (dz < 0) dz += M3;
-                    soff[b][0] = x0 - pr.i0[0];
-                    soff[b][1] = y0 - pr.i0[1];
-                    soff[b][2] = dz;
-                    sq[b] = pr.q;
-                }
-                __syncthreads();
-                // window values at the tile's 8 offsets: one thread per (particle, axis)
-                for (int e = threadIdx.x; e < nb * 3; e += kSpreadThreads) {
-                    const int b = e / 3, a = e - 3 * b;
-                    const T *wrow = wts + (size_t)(b0 + b) * 3 * P + a * P;
-                    const int base = soff[b][a];
-                    const T scale = a == 2 ? sq[b] : (T)1;
-                    T v[kBin];
+        nzb_s = (bx_lo > bx_hi || by_lo > by_hi) ? 0 : nz;
+    }
+    __syncthreads();
+    const int nyb = by_hi - by_lo + 1;
+    const int nrows = min(nzb_s * max(nyb, 0), kSpreadMaxRows);
+    if (threadIdx.x < 32) {
+        // each (z, y) row of bins is one range of the bin-sorted records; their lengths and offsets in
+        // the concatenated list (two rows per lane, one warp scan), loaded in parallel
+        int len[2], beg[2];
 #pragma unroll
-                    for (int o = 0; o < kBin; ++o) {
-                        int rel = base + o;
-                        if (a == 2 && rel >= M3) rel -= M3;
-                        v[o] = (rel >= 0 && rel < P) ? wrow[rel] * scale : (T)0;
-                    }
+        for (int h = 0; h < 2; ++h) {
+            const int r = threadIdx.x + 32 * h;
+            len[h] = 0;
+            beg[h] = 0;
+            if (r < nrows) {
+                const int row = (zbl[r / nyb] * g.nby + by_lo + r % nyb) * g.nbx;
+                beg[h] = bin_start[row + bx_lo];
+                len[h] = bin_start[row + bx_hi + 1] - beg[h];
+            }
+        }
+        int inc0 = len[0], inc1 = len[1];
 #pragma unroll
-                    for (int o = 0; o < kBin; ++o) sw[b][a][o] = v[o];
-                }
-                __syncthreads();
+        for (int o = 1; o < 32; o <<= 1) {
+            const int s0 = __shfl_up_sync(0xffffffffu, inc0, o), s1 = __shfl_up_sync(0xffffffffu, inc1, o);
+            if ((int)threadIdx.x >= o) {
+                inc0 += s0;
+                inc1 += s1;
+            }
+        }
+        const int tot0 = __shfl_sync(0xffffffffu, inc0, 31);
+        rbeg[threadIdx.x] = beg[0];
+        rbeg[threadIdx.x + 32] = beg[1];
+        rpre[threadIdx.x] = inc0 - len[0];
+        rpre[threadIdx.x + 32] = tot0 + inc1 - len[1];
+        if (threadIdx.x == 31) rpre[64] = tot0 + inc1;
+    }
+    __syncthreads();
+    const int total = rpre[nrows];  // rows past nrows have length 0
+    const bool any = total > 0;     // the tile saw a particle (the same for every thread of the CTA)
+    int rcur = 0;                   // this thread's row (its element of each batch only moves forward)
+    static_assert(kSpreadBatch == kSpreadThreads, "one record per thread and batch");
+    for (int v0 = 0; v0 < total; v0 += kSpreadBatch) {
+        const int nb = min(kSpreadBatch, total - v0);
+        __syncthreads();  // previous batch fully consumed
+        if ((int)threadIdx.x < nb) {
+            const int v = v0 + (int)threadIdx.x, b = threadIdx.x;
+            while (rpre[rcur + 1] <= v) ++rcur;
+            const int i = rbeg[rcur] + (v - rpre[rcur]);
+            sidx[b] = i;
+            const PartRec<T> pr = parts[i];
+            // support offset of the tile origin per axis; z taken cyclically into [0, M3), so that
+            // dz + o needs one wrap (a plain difference misses the wrapped part of the support when
+            // M3 < P + 8)
+            int dz = z0 - pr.i0[2];
+            if (dz < 0) dz += M3;
+            soff[b][0] = x0 - pr.i0[0];
+            soff[b][1] = y0 - pr.i0[1];
+            soff[b][2] = dz;
+            sq[b] = pr.q;
+        }
+        __syncthreads();
+        // window values at the tile's 8 offsets: one thread per (particle, axis)
+        for (int e = threadIdx.x; e < nb * 3; e += kSpreadThreads) {
+            const int b = e / 3, a = e - 3 * b;
+            const T *wrow = wts + (size_t)sidx[b] * 3 * P + a * P;
+            const int base = soff[b][a];
+            const T scale = a == 2 ? sq[b] : (T)1;
+            T v[kBin];
+#pragma unroll
+            for (int o = 0; o < kBin; ++o) {
+                int rel = base + o;
+                if (a == 2 && rel >= M3) rel -= M3;
+                v[o] = (rel >= 0 && rel < P) ? wrow[rel] * scale : (T)0;
+            }
+#pragma unroll
+            for (int o = 0; o < kBin; ++o) sw[b][a][o] = v[o];
+        }
+        __syncthreads();
 #pragma unroll 8  // independent particles interleave their shared loads (0.51 -> 0.44 ms at C2)
-                for (int b = grp; b < nb; b += kSpreadGroups) {
-                    const T wz0 = sw[b][2][tz], wz1 = sw[b][2][tz + 1];
-                    const T wy0 = sw[b][1][ty], wy1 = sw[b][1][ty + 1];
-                    const T s00 = wz0 * wy0, s01 = wz0 * wy1, s10 = wz1 * wy0, s11 = wz1 * wy1;
-                    if constexpr (sizeof(T) == 4) {
-                        // packed pairs of x columns: 16 two-wide FMAs instead of 32
-                        const float4 xa = *reinterpret_cast<const float4 *>(&sw[b][0][0]);
-                        const float4 xb = *reinterpret_cast<const float4 *>(&sw[b][0][4]);
-                        const f32x2 w[4] = {f2_pack(xa.x, xa.y), f2_pack(xa.z, xa.w), f2_pack(xb.x, xb.y),
-                                         f2_pack(xb.z, xb.w)};
-                        const f32x2 sp[4] = {f2_splat(s00), f2_splat(s01), f2_splat(s10), f2_splat(s11)};
+        for (int b = grp; b < nb; b += kSpreadGroups) {
+            const T wz0 = sw[b][2][tz], wz1 = sw[b][2][tz + 1];
+            const T wy0 = sw[b][1][ty], wy1 = sw[b][1][ty + 1];
+            const T s00 = wz0 * wy0, s01 = wz0 * wy1, s10 = wz1 * wy0, s11 = wz1 * wy1;
+            if constexpr (sizeof(T) == 4) {
+                // packed pairs of x columns: 16 two-wide FMAs instead of 32
+                const float4 xa = *reinterpret_cast<const float4 *>(&sw[b][0][0]);
+                const float4 xb = *reinterpret_cast<const float4 *>(&sw[b][0][4]);
+                const f32x2 w[4] = {f2_pack(xa.x, xa.y), f2_pack(xa.z, xa.w), f2_pack(xb.x, xb.y),
+                                 f2_pack(xb.z, xb.w)};
+                const f32x2 sp[4] = {f2_splat(s00), f2_splat(s01), f2_splat(s10), f2_splat(s11)};
 #pragma unroll
-                        for (int r = 0; r < 4; ++r)
+                for (int r = 0; r < 4; ++r)
 #pragma unroll
-                            for (int j = 0; j < kBin / 2; ++j) acc2[r][j] = f2_fma(sp[r], w[j], acc2[r][j]);
-                    } else {
+                    for (int j = 0; j < kBin / 2; ++j) acc2[r][j] = f2_fma(sp[r], w[j], acc2[r][j]);
+            } else {
 #pragma unroll
-                        for (int c = 0; c < kBin; ++c) {
-                            const T wx = sw[b][0][c];
-                            acc[0][c] += s00 * wx;
-                            acc[1][c] += s01 * wx;
-                            acc[2][c] += s10 * wx;
-                            acc[3][c] += s11 * wx;
-                        }
-                    }
+                for (int c = 0; c < kBin; ++c) {
+                    const T wx = sw[b][0][c];
+                    acc[0][c] += s00 * wx;
+                    acc[1][c] += s01 * wx;
+                    acc[2][c] += s10 * wx;
+                    acc[3][c] += s11 * wx;
                 }
             }
         }

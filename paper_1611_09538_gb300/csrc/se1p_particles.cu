@@ -587,101 +587,14 @@ __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? kSpreadMinBlo
 
 // ------------------------------------------------------------------ gathering (Eqs. 3.11, 3.25)
 //
-// One warp per particle; lane l handles x offset l of the support (P <= 32),
-// loops over the P x P (z, y) rows with the y and z window values broadcast
-// from shared memory, and the four sums are reduced across the warp.
-template <typename T, int PC>
-__global__ void __launch_bounds__(256) k_gather(Geo g, int n, const PartRec<T> *__restrict__ parts,
-                                                const T *__restrict__ wts, const T *__restrict__ grid,
-                                                double *__restrict__ phi, double *__restrict__ frc,
-                                                int flags, GatherScale sc)
-{
-    // flags: bit 0 adds the self term (Eq. 2.5); bit 1 writes the field -grad phi
-    // instead of the force -q grad phi.
-    // Per warp: y window values interleaved as (wy_j, wy_j dy_j) so that one
-    // 16-byte shared load (float) serves two rows; z values (wz, wz dz) per row.
-    __shared__ __align__(16) T sy[8][34][2];
-    __shared__ T sz[8][2][32];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int P = PC > 0 ? PC : g.P;  // compile-time support width when PC > 0 (loops unroll)
-    const int warps_total = gridDim.x * (blockDim.x >> 5);
-    for (int pi = blockIdx.x * (blockDim.x >> 5) + wib; pi < n; pi += warps_total) {
-        const PartRec<T> r = parts[pi];
-        const T *w = wts + (size_t)pi * 3 * P;
-        T wx = 0, wxd = 0;
-        if (lane < P) {
-            const T jc = (T)(lane - g.c);
-            wx = w[lane];
-            wxd = wx * (r.g[0] - jc);
-            const T wy = w[P + lane], wz = w[2 * P + lane];
-            sy[wib][lane][0] = wy;
-            sy[wib][lane][1] = wy * (r.g[1] - jc);
-            sz[wib][0][lane] = wz;
-            sz[wib][1][lane] = wz * (r.g[2] - jc);
-        } else if (lane < 34 - 0 && lane >= P && lane < 34) {
-            sy[wib][lane][0] = (T)0;  // pad for the paired loads of an odd P
-            sy[wib][lane][1] = (T)0;
-        }
-        __syncwarp();
-        T aphi = 0, afy = 0, afz = 0;
-        if (lane < P) {
-            for (int k = 0; k < P; ++k) {
-                int zk = r.i0[2] + k;
-                if (zk >= g.M3) zk -= g.M3;
-                const int xl = r.i0[0] + lane, nxb = gnxb(g.Mt);
-                T a = 0, b = 0;
-#pragma unroll(PC > 0 ? (PC + 1) / 2 : 1)
-                for (int j = 0; j < P; j += 2) {
-                    T wy0, wd0, wy1, wd1;
-                    if constexpr (sizeof(T) == 4) {
-                        const float4 ww = *reinterpret_cast<const float4 *>(&sy[wib][j][0]);
-                        wy0 = ww.x;
-                        wd0 = ww.y;
-                        wy1 = ww.z;
-                        wd1 = ww.w;
-                    } else {
-                        wy0 = sy[wib][j][0];
-                        wd0 = sy[wib][j][1];
-                        wy1 = sy[wib][j + 1][0];
-                        wd1 = sy[wib][j + 1][1];
-                    }
-                    const T v0 = __ldg(grid + gidx(zk, r.i0[1] + j, xl, g.Mt, nxb));
-                    const T v1 = j + 1 < P ? __ldg(grid + gidx(zk, r.i0[1] + j + 1, xl, g.Mt, nxb)) : (T)0;
-                    a += wy0 * v0;
-                    b += wd0 * v0;
-                    a += wy1 * v1;
-                    b += wd1 * v1;
-                }
-                aphi += sz[wib][0][k] * a;
-                afy += sz[wib][0][k] * b;
-                afz += sz[wib][1][k] * a;
-            }
-        }
-        T vphi = warp_sum(wx * aphi);
-        T vfx = warp_sum(wxd * aphi);
-        T vfy = warp_sum(wx * afy);
-        T vfz = warp_sum(wx * afz);
-        if (lane == 0) {
-            const double qd = (double)r.q;
-            double ph = sc.phi * (double)vphi;
-            if (flags & 1) ph += -2.0 * g.xi / sqrt(kPi) * qd;
-            phi[r.orig] = ph;
-            const double qf = (flags & 2) ? 1.0 : qd;
-            frc[3 * r.orig + 0] = qf * sc.fxy * (double)vfx;
-            frc[3 * r.orig + 1] = qf * sc.fxy * (double)vfy;
-            frc[3 * r.orig + 2] = qf * sc.fz * (double)vfz;
-        }
-        __syncwarp();
-    }
-}
-
 template <typename VT> __device__ __forceinline__ VT make_zero();
 template <> __device__ __forceinline__ float4 make_zero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 template <> __device__ __forceinline__ double2 make_zero<double2>() { return make_double2(0.0, 0.0); }
 __device__ __forceinline__ float dotv(const float *w, float4 v) { return w[0] * v.x + w[1] * v.y + w[2] * v.z + w[3] * v.w; }
 __device__ __forceinline__ double dotv(const double *w, double2 v) { return w[0] * v.x + w[1] * v.y; }
 
-// Vectorised gathering on the x-blocked grid.  A particle's x support [i0, i0 + P) lies in NB blocks
+// Vectorised gathering on the x-blocked grid, for supports of P <= PC points (the loop shapes follow
+// PC, the rows and z levels past P are skipped).  A particle's x support [i0, i0 + P) lies in NB blocks
 // of kXB points starting at block i0 / kXB; a warp request covers two blocks x RG rows x the block's
 // VPB 16-byte vectors (32 lanes: lane = (block of the pair, row, vector)), i.e. two 256-byte runs of
 // consecutive rows, whole 128-byte lines.  Each lane holds the x window values of its V points (zero
@@ -689,8 +602,8 @@ __device__ __forceinline__ double dotv(const double *w, double2 v) { return w[0]
 // weighted by the row's y values (wy, wy dy); the z rows are weighted at the end of each z level.
 // FP32 is compiled for four CTAs per SM (64 registers): with the loads of four z levels in flight the
 // kernel is latency-bound, and 32 resident warps beat 24 (C2 alone 0.356 against 0.407 ms).
-template <typename T, int PC>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_gather_vec(Geo g, int n, const PartRec<T> *__restrict__ parts,
+template <typename T, int PC, bool EXACT>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (PC > 24 ? 3 : 4) : 1) k_gather_vec(Geo g, int n, const PartRec<T> *__restrict__ parts,
                                                     const T *__restrict__ wts, const T *__restrict__ grid,
                                                     double *__restrict__ phi, double *__restrict__ frc,
                                                     int flags, GatherScale sc)
@@ -709,21 +622,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_gather_vec(Geo 
     const int bi = lane / (RG * VPB), rem = lane - bi * (RG * VPB);
     const int r = rem / VPB, qv = rem - r * VPB;  // row within the request, vector within the block row
     const int nxb = gnxb(g.Mt);
+    const int P = EXACT ? PC : g.P;  // support width, P <= PC (a compile-time trip count where P = PC)
     const int warps_total = gridDim.x * (blockDim.x >> 5);
     for (int pi = blockIdx.x * (blockDim.x >> 5) + wib; pi < n; pi += warps_total) {
         const PartRec<T> pr = parts[pi];
-        const T *w = wts + (size_t)pi * 3 * PC;
+        const T *w = wts + (size_t)pi * 3 * P;
         for (int j = lane; j < NJ; j += 32) {
             T wy = 0, wyd = 0;
-            if (j < PC) {
-                wy = w[PC + j];
+            if (j < P) {
+                wy = w[P + j];
                 wyd = wy * (pr.g[1] - (T)(j - g.c));
             }
             sy[wib][0][j] = wy;
             sy[wib][1][j] = wyd;
         }
-        if (lane < PC) {
-            const T wz = w[2 * PC + lane];
+        if (lane < P) {
+            const T wz = w[2 * P + lane];
             sz[wib][0][lane] = wz;
             sz[wib][1][lane] = wz * (pr.g[2] - (T)(lane - g.c));
         }
@@ -736,12 +650,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_gather_vec(Geo 
         for (int bp = 0; bp < NBP; ++bp) {
             const int blk = xb0 + 2 * bp + bi;
             // a block is read when it exists and holds at least one support point
-            ld[bp] = blk < nxb && blk * kXB < pr.i0[0] + PC;
+            ld[bp] = blk < nxb && blk * kXB < pr.i0[0] + P;
             loff[bp] = (blk * g.Mt + pr.i0[1] + r) * kXB + V * qv;
 #pragma unroll
             for (int e = 0; e < V; ++e) {
                 const int rel = blk * kXB + V * qv + e - pr.i0[0];
-                const bool in = rel >= 0 && rel < PC;
+                const bool in = rel >= 0 && rel < P;
                 wx[bp][e] = in ? w[rel] : (T)0;
                 wxd[bp][e] = in ? wx[bp][e] * (pr.g[0] - (T)(rel - g.c)) : (T)0;
             }
@@ -750,7 +664,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_gather_vec(Geo 
         T aphi = 0, afx = 0, afy = 0, afz = 0;
         const size_t plane = (size_t)nxb * g.Mt * kXB;
 #pragma unroll 4  // several z levels' loads in flight
-        for (int k = 0; k < PC; ++k) {
+        for (int k = 0; k < P; ++k) {
             int zk = pr.i0[2] + k;
             if (zk >= g.M3) zk -= g.M3;
             const T *gk = grid + (size_t)zk * plane;
@@ -762,7 +676,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_gather_vec(Geo 
 #pragma unroll
                 for (int bp = 0; bp < NBP; ++bp) {
                     VecT v = make_zero<VecT>();
-                    if (ld[bp] && j < PC) v = *reinterpret_cast<const VecT *>(gk + loff[bp] + rg * RG * kXB);
+                    if (ld[bp] && j < P) v = *reinterpret_cast<const VecT *>(gk + loff[bp] + rg * RG * kXB);
                     const T s1 = dotv(wx[bp], v), s2 = dotv(wxd[bp], v);
                     a += wy * s1;
                     b += wy * s2;
@@ -995,14 +909,16 @@ void launch_gather(se1p_plan *p, int n, const void *grid, double *phi, double *f
     const T *w = (const T *)p->b.wts;
     const T *gr = (const T *)grid;
     const int nt = 32 * warps_per_block;
-    const bool vec = true;  // the x-blocked grid keeps every block row 16-byte aligned
-    if (vec && g.P == 24) k_gather_vec<T, 24><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
-    else if (vec && g.P == 16) k_gather_vec<T, 16><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
-    else if (vec && g.P == 12) k_gather_vec<T, 12><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
-    else if (g.P == 24) k_gather<T, 24><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
-    else if (g.P == 12) k_gather<T, 12><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
-    else if (g.P == 16) k_gather<T, 16><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
-    else k_gather<T, 0><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
+    // the x-blocked grid keeps every block row 16-byte aligned: vector loads for every P (the smallest
+    // compiled bound that holds it; 64 systems with P = 18 gathered 4x faster per point than with
+    // scalar loads)
+    if (g.P == 24) k_gather_vec<T, 24, true><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
+    else if (g.P == 16) k_gather_vec<T, 16, true><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
+    else if (g.P == 12) k_gather_vec<T, 12, true><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
+    else if (g.P < 12) k_gather_vec<T, 12, false><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
+    else if (g.P < 16) k_gather_vec<T, 16, false><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
+    else if (g.P < 24) k_gather_vec<T, 24, false><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
+    else k_gather_vec<T, 32, false><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
 }
 
 void launch_vjp_combine(int n, const double *q, const double *v, const double *Eq, const double *phiv,

@@ -482,8 +482,7 @@ se1p_status se1p_plan_create(const se1p_params *prm, int n_max, se1p_plan **out)
     };
     // z passes: a CTA holds xb_z complex pencils of M3 points (twice, for the Stockham passes); with Mt
     // even each complex pencil carries two real ones
-    p->zpair = p->Mf % 2 == 0;
-    p->xb_z = shrink(pow2_fit(2 * (size_t)p->M3 * cT, 32), (long)p->Mf * p->Mf / (p->zpair ? 2 : 1));
+    p->xb_z = shrink(pow2_fit(2 * (size_t)p->M3 * cT, 32), (long)(p->Mf + 1) / 2 * p->Mf);
     for (int c = 0; c < 3; ++c) {
         const size_t cc = c == 0 ? sizeof(Cx<double>) : cT;
         SlabClass &C = p->cls[c];

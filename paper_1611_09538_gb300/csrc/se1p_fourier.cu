@@ -21,60 +21,7 @@ namespace {
 
 __device__ __forceinline__ int signed_index(int i, int n) { return i <= (n - 1) / 2 ? i : i - n; }
 
-// ---- z forward: CTA = (y, chunk of xb x-values); smem [z][p]
-template <typename T>
-__global__ void k_zfwd(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restrict__ tw, int xb, FastDiv fxb,
-                       const T *__restrict__ grid, Cx<T> *__restrict__ zspec, double *__restrict__ slab0)
-{
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
-    Cx<T> *b = a + (size_t)M3 * xb;
-    const int nxc = (Mt + xb - 1) / xb;
-    const int y = blockIdx.x / nxc, x0 = (blockIdx.x % nxc) * xb;
-    for (int e = threadIdx.x; e < M3 * xb; e += blockDim.x) {
-        const int z = fdiv(e, fxb), p = e - z * xb, x = x0 + p;
-        const T v = x < Mt ? grid[gidx(z, y, x, Mt, gnxb(Mt))] : (T)0;
-        a[e] = cx<T>(v, (T)0);
-    }
-    __syncthreads();
-    // k3 = 0 coefficient, summed to FP64 accuracy from the stored grid values: the blockDim / xb
-    // threads of a pencil take every G-th z; FP32 grids keep each thread's partial sum as an
-    // unevaluated hi + lo pair (TwoSum, exact to ~2^-48), FP64 grids sum directly; the partials
-    // are added in FP64 in a fixed order
-    {
-        __shared__ double part[256];
-        const int G = blockDim.x / xb;  // xb is a power of 2 <= 32 that divides blockDim (256)
-        const int g = threadIdx.x / xb, p = threadIdx.x - g * xb;
-        double sum = 0.0;
-        if constexpr (sizeof(T) == sizeof(double)) {
-            for (int z = g; z < M3; z += G) sum += (double)a[z * xb + p].re;
-        } else {
-            float hi = 0.0f, lo = 0.0f;
-            for (int z = g; z < M3; z += G) {
-                const float v = a[z * xb + p].re;
-                const float t = hi + v, bv = t - hi;
-                lo += (hi - (t - bv)) + (v - bv);
-                hi = t;
-            }
-            sum = (double)hi + (double)lo;
-        }
-        part[threadIdx.x] = sum;
-        __syncthreads();
-        if (g == 0 && x0 + p < Mt) {
-            double tot = 0.0;
-            for (int k = 0; k < G; ++k) tot += part[k * xb + p];
-            slab0[(size_t)y * Mt + x0 + p] = tot;
-        }
-    }
-    __syncthreads();
-    Cx<T> *res = fft_smem<T>(a, b, d, xb, fxb, 1, xb, tw, -1);
-    for (int e = threadIdx.x; e < (K3 - 1) * xb; e += blockDim.x) {
-        const int k1 = fdiv(e, fxb), p = e - k1 * xb, k = 1 + k1, x = x0 + p;
-        if (x < Mt) zspec[((size_t)k * Mt + y) * Mt + x] = res[k * xb + p];
-    }
-}
-
-// ---- z forward on pencil pairs (Mt even): the real pencils 2j and 2j + 1 of a row form one complex
+// ---- z forward on pencil pairs: the real pencils 2j and 2j + 1 of a row form one complex
 // pencil H[2j] + i H[2j + 1] (one aligned two-element load); their spectra follow from its FFT Z by
 // Hermitian symmetry, X_2j[k] = (Z[k] + conj Z[-k]) / 2 and X_2j+1[k] = (Z[k] - conj Z[-k]) / 2i.
 // CTA = (y, chunk of xp pairs); half the FFT work and shared memory per real pencil.
@@ -98,7 +45,9 @@ __global__ void k_zfwd_pair(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__re
     __shared__ __align__(8) unsigned long long bar;
     Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
     Cx<T> *b = a + (size_t)M3 * xp;
-    const int npair = Mt / 2, nxc = (npair + xp - 1) / xp;
+    // pencils 2j and 2j + 1; for odd Mt the last pair's second pencil is x = Mt, the x-blocked grid's
+    // zero padding, whose spectra are not stored
+    const int npair = (Mt + 1) / 2, nxc = (npair + xp - 1) / xp;
     const int y = blockIdx.x / nxc, j0 = (blockIdx.x % nxc) * xp;
     if (tma) {
         const unsigned bar_a = smem_addr(&bar);
@@ -164,7 +113,7 @@ __global__ void k_zfwd_pair(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__re
                 ti += part[1][k * xp + pp];
             }
             slab0[(size_t)y * Mt + 2 * (j0 + pp)] = tr;
-            slab0[(size_t)y * Mt + 2 * (j0 + pp) + 1] = ti;
+            if (2 * (j0 + pp) + 1 < Mt) slab0[(size_t)y * Mt + 2 * (j0 + pp) + 1] = ti;
         }
     }
     __syncthreads();
@@ -175,7 +124,7 @@ __global__ void k_zfwd_pair(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__re
             const Cx<T> zk = res[k * xp + pp], zm = res[(M3 - k) * xp + pp];
             Cx<T> *dst = zspec + ((size_t)k * Mt + y) * Mt + 2 * j;
             dst[0] = cx<T>((zk.re + zm.re) * (T)0.5, (zk.im - zm.im) * (T)0.5);
-            dst[1] = cx<T>((zk.im + zm.im) * (T)0.5, (zm.re - zk.re) * (T)0.5);
+            if (2 * j + 1 < Mt) dst[1] = cx<T>((zk.im + zm.im) * (T)0.5, (zm.re - zk.re) * (T)0.5);
         }
     }
 }
@@ -272,41 +221,9 @@ __global__ void k_xinv(int Mt, int ns, int kfirst, int nrows, FftDesc d, const T
     }
 }
 
-// ---- z inverse: Hermitian completion along z, inverse FFT, real part
-template <typename T>
-__global__ void k_zinv(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restrict__ tw, int xb, FastDiv fxb,
-                       const Cx<T> *__restrict__ zspec, const double *__restrict__ slab0, T *__restrict__ grid)
-{
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
-    Cx<T> *b = a + (size_t)M3 * xb;
-    const int nxc = (Mt + xb - 1) / xb;
-    const int y = blockIdx.x / nxc, x0 = (blockIdx.x % nxc) * xb;
-    for (int e = threadIdx.x; e < M3 * xb; e += blockDim.x) {
-        const int k = fdiv(e, fxb), p = e - k * xb, x = x0 + p;
-        Cx<T> v = cx<T>((T)0, (T)0);
-        if (x < Mt) {
-            if (k == 0) {
-                v = cx<T>((T)slab0[(size_t)y * Mt + x], (T)0);
-            } else if (k < K3) {
-                v = zspec[((size_t)k * Mt + y) * Mt + x];
-            } else {
-                const Cx<T> c = zspec[((size_t)(M3 - k) * Mt + y) * Mt + x];
-                v = cx<T>(c.re, -c.im);
-            }
-        }
-        a[e] = v;
-    }
-    __syncthreads();
-    Cx<T> *res = fft_smem<T>(a, b, d, xb, fxb, 1, xb, tw, +1);
-    for (int e = threadIdx.x; e < M3 * xb; e += blockDim.x) {
-        const int z = fdiv(e, fxb), p = e - z * xb, x = x0 + p;
-        if (x < Mt) grid[gidx(z, y, x, Mt, gnxb(Mt))] = res[e].re;
-    }
-}
-
-// ---- z inverse on pencil pairs (Mt even): Z = X_2j + i X_2j+1 over the Hermitian-completed spectra;
-// the real and imaginary parts of its inverse FFT are the pencils 2j and 2j + 1
+// ---- z inverse on pencil pairs: Z = X_2j + i X_2j+1 over the Hermitian-completed spectra; the real and
+// imaginary parts of its inverse FFT are the pencils 2j and 2j + 1 (for odd Mt the last pair has
+// X_Mt = 0 and stores only its real part, so that the grid's padding stays exactly zero)
 template <typename T>
 __global__ void k_zinv_pair(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__restrict__ tw, int xp, FastDiv fxp,
                             const Cx<T> *__restrict__ zspec, const double *__restrict__ slab0, T *__restrict__ grid)
@@ -315,24 +232,25 @@ __global__ void k_zinv_pair(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__re
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Cx<T> *a = reinterpret_cast<Cx<T> *>(smem_raw);
     Cx<T> *b = a + (size_t)M3 * xp;
-    const int npair = Mt / 2, nxc = (npair + xp - 1) / xp;
+    const int npair = (Mt + 1) / 2, nxc = (npair + xp - 1) / xp;
     const int y = blockIdx.x / nxc, j0 = (blockIdx.x % nxc) * xp;
     for (int e = threadIdx.x; e < M3 * xp; e += blockDim.x) {
         const int k = fdiv(e, fxp), pp = e - k * xp, j = j0 + pp;
         Cx<T> v = cx<T>((T)0, (T)0);
         if (j < npair) {
-            Cx<T> xe, xo;
+            const bool odd = 2 * j + 1 < Mt;  // the pair has its second pencil
+            Cx<T> xe, xo = cx<T>((T)0, (T)0);
             if (k == 0) {
                 xe = cx<T>((T)slab0[(size_t)y * Mt + 2 * j], (T)0);
-                xo = cx<T>((T)slab0[(size_t)y * Mt + 2 * j + 1], (T)0);
+                if (odd) xo = cx<T>((T)slab0[(size_t)y * Mt + 2 * j + 1], (T)0);
             } else if (k < K3) {
                 const Cx<T> *src = zspec + ((size_t)k * Mt + y) * Mt + 2 * j;
                 xe = src[0];
-                xo = src[1];
+                if (odd) xo = src[1];
             } else {
                 const Cx<T> *src = zspec + ((size_t)(M3 - k) * Mt + y) * Mt + 2 * j;
                 xe = cx<T>(src[0].re, -src[0].im);
-                xo = cx<T>(src[1].re, -src[1].im);
+                if (odd) xo = cx<T>(src[1].re, -src[1].im);
             }
             v = cx<T>(xe.re - xo.im, xe.im + xo.re);
         }
@@ -343,10 +261,15 @@ __global__ void k_zinv_pair(int M3, int Mt, int K3, FftDesc d, const Tw<T> *__re
     for (int e = threadIdx.x; e < M3 * xp; e += blockDim.x) {
         const int z = fdiv(e, fxp), pp = e - z * xp, j = j0 + pp;
         if (j < npair) {
-            V2 o;
-            o.x = res[e].re;
-            o.y = res[e].im;
-            *reinterpret_cast<V2 *>(grid + gidx(z, y, 2 * j, Mt, gnxb(Mt))) = o;
+            T *dst = grid + gidx(z, y, 2 * j, Mt, gnxb(Mt));
+            if (2 * j + 1 < Mt) {
+                V2 o;
+                o.x = res[e].re;
+                o.y = res[e].im;
+                *reinterpret_cast<V2 *>(dst) = o;
+            } else {
+                dst[0] = res[e].re;
+            }
         }
     }
 }
@@ -459,7 +382,7 @@ template <typename T> void make_zfwd_tensor_map(se1p_plan *p)
     p->tma_zfwd = false;
     const int Mt = p->Mf, M3 = p->M3, xp = p->xb_z, nxb = gnxb(Mt);
     const int bx = 2 * xp < kXB ? 2 * xp : kXB, bxb = 2 * xp < kXB ? 1 : 2 * xp / kXB;
-    if (!p->zpair || (bx * sizeof(T)) % 16 != 0 || (2 * xp) % bx != 0 || bxb > 256) return;
+    if ((bx * sizeof(T)) % 16 != 0 || (2 * xp) % bx != 0 || bxb > 256) return;
     int zbox = 1;
     for (int v = 1; v <= 256 && v <= M3; ++v)
         if (M3 % v == 0) zbox = v;
@@ -496,10 +419,8 @@ template <typename T> int configure_fourier_kernels(se1p_plan *p)
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaError_t e = cudaSuccess;
-    e = (cudaError_t)(e | allow_max_dynamic_smem(k_zfwd<T>, maxsm));
     e = (cudaError_t)(e | allow_max_dynamic_smem(k_zfwd_pair<T>, maxsm));
     e = (cudaError_t)(e | allow_max_dynamic_smem(k_zinv_pair<T>, maxsm));
-    e = (cudaError_t)(e | allow_max_dynamic_smem(k_zinv<T>, maxsm));
     e = (cudaError_t)(e | allow_max_dynamic_smem(k_xfwd<T, false>, maxsm));
     e = (cudaError_t)(e | allow_max_dynamic_smem(k_xinv<T, false>, maxsm));
     e = (cudaError_t)(e | allow_max_dynamic_smem(k_yscale<T, false>, maxsm));
@@ -518,18 +439,11 @@ template <typename T> void launch_fourier(se1p_plan *p, cudaStream_t s)
     {
         const int xb = p->xb_z;
         const size_t sm = 2 * (size_t)M3 * xb * cbytes<T>();
-        if (p->zpair) {  // xb pencil pairs per CTA
-            const int nxc = (Mt / 2 + xb - 1) / xb;
-            k_zfwd_pair<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb,
-                                                     make_fastdiv(xb), (const T *)p->b.gridf, (Cx<T> *)p->b.zspec,
-                                                     p->b.slab0_in, p->tm_zfwd, p->tma_zfwd ? 1 : 0, p->tma_zbox,
-                                                     p->b.status, p->spin_limit);
-        } else {
-            const int nxc = (Mt + xb - 1) / xb;
-            k_zfwd<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb,
-                                                make_fastdiv(xb), (const T *)p->b.gridf, (Cx<T> *)p->b.zspec,
-                                                p->b.slab0_in);
-        }
+        const int nxc = ((Mt + 1) / 2 + xb - 1) / xb;  // xb pencil pairs per CTA
+        k_zfwd_pair<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb, make_fastdiv(xb),
+                                                 (const T *)p->b.gridf, (Cx<T> *)p->b.zspec, p->b.slab0_in,
+                                                 p->tm_zfwd, p->tma_zfwd ? 1 : 0, p->tma_zbox, p->b.status,
+                                                 p->spin_limit);
     }
     // the three slab classes are independent between the z passes: classes 0 (k3 = 0, FP64)
     // and 1 (set I) run on the plan's two Fourier streams, class 2 (set J) on s
@@ -578,17 +492,9 @@ template <typename T> void launch_fourier(se1p_plan *p, cudaStream_t s)
     {
         const int xb = p->xb_z;
         const size_t sm = 2 * (size_t)M3 * xb * cbytes<T>();
-        if (p->zpair) {
-            const int nxc = (Mt / 2 + xb - 1) / xb;
-            k_zinv_pair<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb,
-                                                     make_fastdiv(xb), (const Cx<T> *)p->b.zspec, p->b.slab0_out,
-                                                     (T *)p->b.gridf);
-        } else {
-            const int nxc = (Mt + xb - 1) / xb;
-            k_zinv<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb,
-                                                make_fastdiv(xb), (const Cx<T> *)p->b.zspec, p->b.slab0_out,
-                                                (T *)p->b.gridf);
-        }
+        const int nxc = ((Mt + 1) / 2 + xb - 1) / xb;
+        k_zinv_pair<T><<<Mt * nxc, 256, sm, s>>>(M3, Mt, K3, p->fd_z, (const Tw<T> *)p->b.tw_z, xb, make_fastdiv(xb),
+                                                 (const Cx<T> *)p->b.zspec, p->b.slab0_out, (T *)p->b.gridf);
     }
 }
 

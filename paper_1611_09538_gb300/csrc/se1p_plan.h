@@ -68,13 +68,13 @@ struct se1p_plan {
     int Mf = 0;
     bool per3 = false;
     se1p::FftDesc fd_z{};
-    int xb_z = 1;      // z passes: pencils per CTA, or pencil pairs per CTA when zpair
+    int xb_z = 1;      // z passes: pencil pairs per CTA (two real pencils as one complex pencil; for odd
+                       // Mf the last pencil pairs with the zero padding of the x-blocked grid)
     // z forward pass by bulk tensor copies (tma_zfwd) of zbox-deep boxes; polls of its bounded wait
     CUtensorMap tm_zfwd{};
     bool tma_zfwd = false;
     int tma_zbox = 0;
     long long spin_limit = 1ll << 22;
-    bool zpair = false;  // Mt even: the z passes transform two real pencils as one complex pencil
     se1p::SlabClass cls[3];  // 0: k3 = 0 (FP64 always), 1: I, 2: J
     se1p::Buffers b;
     std::vector<void *> dev_allocs;

@@ -120,11 +120,26 @@ __global__ void k_pack(Geo g, int n, const double *__restrict__ x, const double 
         sq = qq;
         saq = fabs(qq);
     }
+    // the CTA's charge sums, then one pair of atomic adds per CTA (per warp, the two addresses
+    // received thousands of same-address atomics per evaluation)
+    __shared__ double ws[2][32];
     sq = warp_sum(sq);
     saq = warp_sum(saq);
-    if ((threadIdx.x & 31) == 0 && (sq != 0.0 || saq != 0.0)) {
-        atomicAdd(sums, sq);
-        atomicAdd(sums + 1, saq);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+        ws[0][w] = sq;
+        ws[1][w] = saq;
+    }
+    __syncthreads();
+    if (w == 0) {
+        sq = lane < nw ? ws[0][lane] : 0.0;
+        saq = lane < nw ? ws[1][lane] : 0.0;
+        sq = warp_sum(sq);
+        saq = warp_sum(saq);
+        if (lane == 0 && (sq != 0.0 || saq != 0.0)) {
+            atomicAdd(sums, sq);
+            atomicAdd(sums + 1, saq);
+        }
     }
 }
 

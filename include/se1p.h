@@ -176,8 +176,9 @@ se1p_status se1p_gather(se1p_plan *plan, int n, const double *x, const double *q
                         const double *grid, double *phi, double *force, void *stream);
 
 /* Real-space part, Eq. 2.2 and its force (Eq. 3.22), over a cell list whose cells
- * have an edge of at least rc/3 (a target's sources lie within ceil(rc / edge)
- * cells per axis).  Writes (does not accumulate) phi and force.  Requires
+ * have an edge of at least rc/3 where a particle expects at least 800 neighbours
+ * within rc (n_max at uniform density), rc/2 otherwise (a target's sources lie
+ * within ceil(rc / edge) cells per axis).  Writes (does not accumulate) phi and force.  Requires
  * params.rc > 0 and rc <= L3. */
 se1p_status se1p_real_space(se1p_plan *plan, int n, const double *x, const double *q, double *phi,
                             double *force, void *stream);

@@ -17,6 +17,9 @@ constexpr int kRealWarps = 4;  // warps per CTA (warps work independently)
 // rc = 0.15 (~1400 expected neighbours): 1.528 ms with four, 1.543 with two; N = 10^6 in [1,1,8],
 // rc = 0.09 (~380): 12.42 ms with four, 12.32 with two.
 constexpr double kRealSplitNeighbours = 800.0;
+// One warp per target group below this (64 systems of ~230 expected neighbours: 14.86 -> 14.78 ms;
+// N = 10^6 in [1, 1, 8] with ~380 keeps two: 10.57 against 10.60 ms with one)
+constexpr double kRealOneWarpNeighbours = 300.0;
 // CTAs per SM the FP32 kernel is compiled for (72 registers per thread): with the unrolled candidate
 // test the compiler would take 96 and fit five; seven are faster (C2, stage alone: 0.83 against 0.96 ms)
 constexpr int kCand = 96;      // per-warp candidate list (flushed at >= 64)
@@ -533,6 +536,10 @@ void launch_real_space(se1p_plan *p, int n, const int *cell_key, double *phi, do
         const int blocks = (groups * 4 + kRealWarps - 1) / kRealWarps;
         if (g.per3) k_real<T, 4, true><<<blocks, 32 * kRealWarps, 0, s>>>(g, n, starts, cells, cell_key, phi, frc, accumulate, rsum);
         else k_real<T, 4, false><<<blocks, 32 * kRealWarps, 0, s>>>(g, n, starts, cells, cell_key, phi, frc, accumulate, rsum);
+    } else if (neighbours < kRealOneWarpNeighbours) {
+        const int blocks = (groups + kRealWarps - 1) / kRealWarps;
+        if (g.per3) k_real<T, 1, true><<<blocks, 32 * kRealWarps, 0, s>>>(g, n, starts, cells, cell_key, phi, frc, accumulate, rsum);
+        else k_real<T, 1, false><<<blocks, 32 * kRealWarps, 0, s>>>(g, n, starts, cells, cell_key, phi, frc, accumulate, rsum);
     } else {
         const int blocks = (groups * 2 + kRealWarps - 1) / kRealWarps;
         if (g.per3) k_real<T, 2, true><<<blocks, 32 * kRealWarps, 0, s>>>(g, n, starts, cells, cell_key, phi, frc, accumulate, rsum);

@@ -17,8 +17,9 @@ namespace {
 
 constexpr double kShapeC = 0.95;  // Gaussian shape constant c of Eq. 3.3
 // shared memory per Fourier-pass CTA: small enough that the passes find room on SMs that the
-// concurrent real space occupies (measured at N = 10^6, M3 = 1024: 48 KB 12.33 ms, 96 KB 12.42 ms)
-constexpr size_t kSmemBudget = 48 * 1024;
+// concurrent real space occupies (measured at N = 10^6, M3 = 1024: 32 / 48 / 64 / 96 KB 10.59 / 10.56 /
+// 10.45 / 10.60 ms; 64 systems 15.24 / 14.73 / 14.72 / 15.42 ms; N = 10^5 unchanged)
+constexpr size_t kSmemBudget = 64 * 1024;
 
 bool is_smooth(long n)
 {

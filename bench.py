@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--table-6-1-ratio", action="store_true",
                     help="k-space runtime of SE1P over the triply periodic SE3P on the systems of Table 6.1 "
                          "(Example 6.5), then exit")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the 64-system batch (warm-up + timed graph launches, no one-by-one "
+                         "comparison; for ncu launch lists); prints a short line")
     ap.add_argument("--profile-only", action="store_true",
                     help="only warm-up + timed steps (for ncu launch lists); prints a short line")
     return ap.parse_args()
@@ -566,7 +569,7 @@ def measure_vjp(plan, n, x, q, stream, steps, precision):
             "status": se1p.STATUS.get(st), "what": "se1p_eval_vjp: dl/dx and dl/dq for a cotangent of phi"}
 
 
-def measure_batched(stream, steps=5):
+def measure_batched(stream, steps=5, warmup=2, sequential=True):
     """64 independent neutral systems (N log-uniform in [1k, 50k], L = [1,1,Lz], Lz in [1,4],
     xi = 20, parameters from se1p_autotune at rms 1e-6, mixed precision), one graph launch
     per step."""
@@ -583,7 +586,7 @@ def measure_batched(stream, steps=5):
     F = torch.empty((ntot, 3), dtype=torch.float64, device="cuda")
     E = torch.empty(len(systems), dtype=torch.float64, device="cuda")
     b = se1p.se1p_batch_create(params, [len(s.q) for s in systems])
-    for _ in range(2):
+    for _ in range(warmup):
         se1p.se1p_batch_eval(b, offsets, x, q, phi, F, E, stream)
     st = se1p.se1p_batch_sync_status(b, stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -597,7 +600,7 @@ def measure_batched(stream, steps=5):
     # the same systems evaluated one after another through their own plans (no graph, no overlap):
     # how much the single graph launch gains from running systems side by side
     seq = 0.0
-    for i in range(len(systems)):
+    for i in range(len(systems) if sequential else 0):
         o, m = int(offsets[i]), int(offsets[i + 1] - offsets[i])
         h = se1p.se1p_batch_plan(b, i)
         for _ in range(2):
@@ -612,7 +615,7 @@ def measure_batched(stream, steps=5):
     se1p.se1p_batch_destroy(b)
     return {"value": ntot / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "systems": len(systems),
             "particles": ntot, "status": se1p.STATUS.get(st), "precision": "mixed",
-            "sequential_ms_per_step": seq,
+            "sequential_ms_per_step": seq if sequential else None,
             "workload": "64 systems, N log-uniform in [1k,50k], L=[1,1,Lz], Lz~U[1,4], xi=20, "
                         "autotuned at rms 1e-6, one CUDA-graph launch per step"}
 
@@ -841,6 +844,14 @@ def main():
         table_6_2(args)
     elif args.table_6_1_ratio:
         table_6_1_ratio(args)
+    elif args.batched_only:
+        import torch
+        from paper_1611_09538_gb300 import build as lib_build
+        lib_build.build()
+        torch.cuda.set_device(local_rank)
+        stream = torch.cuda.current_stream()
+        print(json.dumps(measure_batched(stream, steps=args.steps, warmup=args.warmup, sequential=False)),
+              flush=True)
     else:
         run_gpu(args, rank, world, local_rank)
 

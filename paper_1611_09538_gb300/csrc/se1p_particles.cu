@@ -422,6 +422,9 @@ __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? kSpreadMinBlo
     const int grp = threadIdx.x >> 4, tl = threadIdx.x & 15;
     const int tz = 2 * (tl >> 2), ty = 2 * (tl & 3);  // this thread's z and y pairs
     const int P = g.P, M3 = g.M3;
+    // FP32 window rows fetched as aligned 16-byte chunks (P % 4 == 0); the z rows so only where the
+    // support cannot wrap onto itself within a tile (M3 >= P + 8)
+    const bool vec_rows = (P & 3) == 0, short_z = M3 < P + kBin;
     T acc[4][kBin];  // [2 dz + dy][x]
 #pragma unroll
     for (int r = 0; r < 4; ++r)
@@ -522,12 +525,48 @@ __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? kSpreadMinBlo
             sq[b] = pr.q;
         }
         __syncthreads();
-        // window values at the tile's 8 offsets: one thread per (particle, axis)
+        // window values at the tile's 8 offsets: one thread per (particle, axis), i.e. per row
+        // e = 3 b + a of sw
         for (int e = threadIdx.x; e < nb * 3; e += kSpreadThreads) {
             const int b = e / 3, a = e - 3 * b;
             const T *wrow = wts + (size_t)sidx[b] * 3 * P + a * P;
             const int base = soff[b][a];
             const T scale = a == 2 ? sq[b] : (T)1;
+            if constexpr (sizeof(T) == 4) {
+                if (vec_rows && (a < 2 || !short_z)) {
+                    // the rows are 16-byte aligned (P % 4 == 0): the 8 offsets lie in three aligned
+                    // 4-value chunks from the first offset rounded down, each wholly inside [0, P) or
+                    // outside it; on the z axis an offset past M3 - 8 means the wrapped part of the
+                    // support, which (M3 >= P + 8) starts before it, at base - M3 in [-7, -1]
+                    const int bs = (a == 2 && base > M3 - kBin) ? base - M3 : base;
+                    const int c = bs & ~3, sh = bs & 3;
+                    float u[12];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const int ck = c + 4 * k;
+                        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (ck >= 0 && ck < P) t = *reinterpret_cast<const float4 *>(wrow + ck);
+                        u[4 * k] = t.x;
+                        u[4 * k + 1] = t.y;
+                        u[4 * k + 2] = t.z;
+                        u[4 * k + 3] = t.w;
+                    }
+                    float u2[10], w[kBin];
+#pragma unroll
+                    for (int o = 0; o < 10; ++o) u2[o] = (sh & 2) ? u[o + 2] : u[o];
+#pragma unroll
+                    for (int o = 0; o < kBin; ++o) w[o] = ((sh & 1) ? u2[o + 1] : u2[o]) * scale;
+                    // two 16-byte stores per 32-byte row; rows e and e + 4 (the same banks) store
+                    // opposite halves first, so each quarter-warp phase covers the 32 banks once
+                    const float4 lo = make_float4(w[0], w[1], w[2], w[3]);
+                    const float4 hi = make_float4(w[4], w[5], w[6], w[7]);
+                    const int h = (e >> 2) & 1;
+                    float4 *dst = reinterpret_cast<float4 *>(&sw[b][a][0]);
+                    dst[h] = h ? hi : lo;
+                    dst[h ^ 1] = h ? lo : hi;
+                    continue;
+                }
+            }
             T v[kBin];
 #pragma unroll
             for (int o = 0; o < kBin; ++o) {

@@ -197,6 +197,7 @@ template <typename T> se1p_status alloc_particles(se1p_plan *p, Alloc &A)
     p->b.starts = (int *)A.dev(sizeof(int) * (size_t)(g.nbins + g.ncells + 2));
     p->b.cursors = (int *)A.dev(sizeof(int) * (size_t)(g.nbins + g.ncells));
     p->b.scan_tmp = (int *)A.dev(sizeof(int) * (size_t)kScanTmp);
+    p->b.gchunk = (int *)A.dev(sizeof(int) * (size_t)kGatherChunks);
     p->b.parts = A.dev(sizeof(PartRec<T>) * (size_t)nm);
     p->b.wts = A.dev(sizeof(T) * 3 * (size_t)p->geo.P * nm);
     p->b.cells = A.dev(sizeof(CellRec<T>) * (size_t)nm);
@@ -512,6 +513,7 @@ se1p_status se1p_plan_create(const se1p_params *prm, int n_max, se1p_plan **out)
     if (st == SE1P_OK) st = mixed ? build_tables<float>(p, A) : build_tables<double>(p, A);
     if (st != SE1P_OK) { free_all(p); delete p; return st; }
     int cfg = mixed ? configure_fourier_kernels<float>(p) : configure_fourier_kernels<double>(p);
+    if (cfg == 0) cfg = mixed ? configure_particle_kernels<float>(p) : configure_particle_kernels<double>(p);
     if (cfg != 0) { cudaGetLastError(); free_all(p); delete p; return SE1P_ERR_CUDA; }
     bool streams_ok = cudaStreamCreateWithFlags(&p->s_real, cudaStreamNonBlocking) == cudaSuccess &&
                       cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) == cudaSuccess &&

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "se1p_plan.h"
@@ -647,6 +648,88 @@ template <> __device__ __forceinline__ double2 make_zero<double2>() { return mak
 __device__ __forceinline__ float dotv(const float *w, float4 v) { return w[0] * v.x + w[1] * v.y + w[2] * v.z + w[3] * v.w; }
 __device__ __forceinline__ double dotv(const double *w, double2 v) { return w[0] * v.x + w[1] * v.y; }
 
+__device__ __forceinline__ int sm_id()
+{
+    int v;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(v));
+    return v;
+}
+
+// Particle handout of the gather, for long particle lists.  The bin-sorted particles form chunks of
+// 2^sh consecutive ones, and sequence q is made of the chunks q, q + nseq, q + 2 nseq, ... (one sequence
+// per SM).  A warp starts on the sequence of its SM, so the warps of one SM read neighbouring supports
+// at the same time and find them in L1 (with a fixed stride over the particles, the CTAs of an SM
+// worked on unrelated parts of the grid: L1 hit rate 66 %), and all SMs move through the grid together,
+// so that the part of the grid in use stays in L2 (one contiguous chunk per SM kept the whole grid in
+// use at once: with 10^6 particles on 128 x 128 x 1024 points the L2 hit rate fell to 62 %).  Once
+// its sequence is used up a warp moves to the sequence with the most particles left.  Every index is
+// handed out once, by an atomic add on the sequence's cursor; no warp waits for another.  A warp's
+// current sequence sits in shared memory (st[0]), where it costs the gather's loop no registers.
+struct ChunkArgs {
+    int *next;   // cursor of each sequence
+    int nseq;    // sequences, 0: no handout (warp w takes the particles w, w + warps, ...)
+    int nchunk;  // chunks
+    int sh;      // log2 of the chunk length
+    int n;
+};
+
+__device__ __forceinline__ int chunk_claim(const ChunkArgs &c, const int *st, int lane)
+{
+    return lane == 0 ? atomicAdd(c.next + st[0], 1) : 0;
+}
+
+// the particle of the t-th claim on sequence q (n or more once the sequence is used up)
+__device__ __forceinline__ int seq_particle(const ChunkArgs &c, int q, int t)
+{
+    return ((q + c.nseq * (t >> c.sh)) << c.sh) + (t & ((1 << c.sh) - 1));
+}
+
+__device__ __forceinline__ void chunk_set(int *st, int q, int lane)
+{
+    __syncwarp();
+    if (lane == 0) st[0] = q;
+    __syncwarp();
+}
+
+// the current sequence is used up: claim from the one with the most left (all cursors read at once,
+// in L2, where the atomics act); -1 when every sequence is used up
+__device__ __forceinline__ int chunk_refill(const ChunkArgs &c, int *st, int lane)
+{
+    while (true) {
+        int left = 0, best = -1;
+        for (int q = lane; q < c.nseq; q += 32) {
+            // particles of sequence q: its chunks, the last chunk of the list possibly short
+            const int cnt = q < c.nchunk ? (c.nchunk - 1 - q) / c.nseq + 1 : 0;
+            int len = cnt << c.sh;
+            if (cnt > 0 && (c.nchunk - 1) % c.nseq == q) len -= ((c.nchunk) << c.sh) - c.n;
+            const int l = len - __ldcg(c.next + q);
+            if (l > left) {
+                left = l;
+                best = q;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int ol = __shfl_xor_sync(0xffffffffu, left, o), ob = __shfl_xor_sync(0xffffffffu, best, o);
+            if (ol > left || (ol == left && ob > best)) {
+                left = ol;
+                best = ob;
+            }
+        }
+        if (left <= 0) return -1;
+        chunk_set(st, best, lane);
+        const int pi = seq_particle(c, best, __shfl_sync(0xffffffffu, chunk_claim(c, st, lane), 0));
+        if (pi < c.n) return pi;
+    }
+}
+
+// the particle of a claim made earlier, else one of another sequence, else -1
+__device__ __forceinline__ int chunk_take(const ChunkArgs &c, int *st, int ticket, int lane)
+{
+    const int pi = seq_particle(c, st[0], __shfl_sync(0xffffffffu, ticket, 0));
+    return pi < c.n ? pi : chunk_refill(c, st, lane);
+}
+
 // Vectorised gathering on the x-blocked grid, for supports of P <= PC points (the loop shapes follow
 // PC, the rows and z levels past P are skipped).  A particle's x support [i0, i0 + P) lies in NB blocks
 // of kXB points starting at block i0 / kXB; a warp request covers two blocks x RG rows x the block's
@@ -656,11 +739,11 @@ __device__ __forceinline__ double dotv(const double *w, double2 v) { return w[0]
 // weighted by the row's y values (wy, wy dy); the z rows are weighted at the end of each z level.
 // FP32 is compiled for four CTAs per SM (64 registers): with the loads of four z levels in flight the
 // kernel is latency-bound, and 32 resident warps beat 24 (C2 alone 0.356 against 0.407 ms).
-template <typename T, int PC, bool EXACT>
+template <typename T, int PC, bool EXACT, bool HANDOUT>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (PC > 24 ? 3 : 4) : 1) k_gather_vec(Geo g, int n, const PartRec<T> *__restrict__ parts,
                                                     const T *__restrict__ wts, const T *__restrict__ grid,
                                                     double *__restrict__ phi, double *__restrict__ frc,
-                                                    int flags, GatherScale sc)
+                                                    int flags, GatherScale sc, ChunkArgs ca)
 {
     constexpr int V = 16 / sizeof(T);                    // values per 16-byte vector
     constexpr int VPB = kXB / V;                         // vectors per block row
@@ -677,8 +760,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (PC > 24 ? 3 : 4) : 1) k
     const int r = rem / VPB, qv = rem - r * VPB;  // row within the request, vector within the block row
     const int nxb = gnxb(g.Mt);
     const int P = EXACT ? PC : g.P;  // support width, P <= PC (a compile-time trip count where P = PC)
+    __shared__ int sst[8];
+    int *st = sst + wib;
     const int warps_total = gridDim.x * (blockDim.x >> 5);
-    for (int pi = blockIdx.x * (blockDim.x >> 5) + wib; pi < n; pi += warps_total) {
+    int pi = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (HANDOUT) {
+        chunk_set(st, sm_id() % ca.nseq, lane);
+        pi = chunk_take(ca, st, chunk_claim(ca, st, lane), lane);
+    }
+    while (pi >= 0 && pi < n) {
+        // the next particle, claimed now and read after this one
+        const int ticket = HANDOUT ? chunk_claim(ca, st, lane) : 0;
         const PartRec<T> pr = parts[pi];
         const T *w = wts + (size_t)pi * 3 * P;
         for (int j = lane; j < NJ; j += 32) {
@@ -755,6 +847,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (PC > 24 ? 3 : 4) : 1) k
             frc[3 * pr.orig + 2] = qf * sc.fz * (double)vfz;
         }
         __syncwarp();
+        pi = HANDOUT ? chunk_take(ca, st, ticket, lane) : pi + warps_total;
     }
 }
 
@@ -943,12 +1036,53 @@ template <typename T> void launch_spread(se1p_plan *p, cudaStream_t s)
 }
 
 template <typename T>
+using GatherKernel = void (*)(Geo, int, const PartRec<T> *, const T *, const T *, double *, double *, int, GatherScale,
+                              ChunkArgs);
+
+// the x-blocked grid keeps every block row 16-byte aligned: vector loads for every P (the smallest
+// compiled bound that holds it; 64 systems with P = 18 gathered 4x faster per point than with
+// scalar loads)
+template <typename T, bool H> GatherKernel<T> gather_kernel_h(int P)
+{
+    if (P == 24) return k_gather_vec<T, 24, true, H>;
+    if (P == 16) return k_gather_vec<T, 16, true, H>;
+    if (P == 12) return k_gather_vec<T, 12, true, H>;
+    if (P < 12) return k_gather_vec<T, 12, false, H>;
+    if (P < 16) return k_gather_vec<T, 16, false, H>;
+    if (P < 24) return k_gather_vec<T, 24, false, H>;
+    return k_gather_vec<T, 32, false, H>;
+}
+template <typename T> GatherKernel<T> gather_kernel(int P, bool handout)
+{
+    return handout ? gather_kernel_h<T, true>(P) : gather_kernel_h<T, false>(P);
+}
+
+constexpr int kGatherWarps = 8;  // warps per CTA, one particle each at a time
+// the handout pays where each resident warp gathers at least this many particles; shorter lists take
+// one particle per warp, with no atomics (64 systems of 1000 to 50 000 particles: 15.10 against
+// 14.63 ms with every list handed out)
+constexpr int kGatherHandoutPerWarp = 16;
+
+template <typename T>
 void launch_gather(se1p_plan *p, int n, const void *grid, double *phi, double *frc, int flags, cudaStream_t s)
 {
     if (n <= 0) return;
-    const int warps_per_block = 8;
-    int blocks = (n + warps_per_block - 1) / warps_per_block;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    ChunkArgs ca;
+    ca.next = p->b.gchunk;
+    ca.n = n;
+    ca.nseq = 0;
+    ca.nchunk = 0;
+    ca.sh = 0;
+    int blocks = (n + kGatherWarps - 1) / kGatherWarps;  // one particle per warp
+    if ((long long)n >= (long long)kGatherHandoutPerWarp * kGatherWarps * p->gather_ctas) {
+        // as many CTAs as are resident at once; chunks of n / SMs particles rounded down to a power of
+        // two in [64, 1024] (N = 10^5 on 96^2 x 64 points: 512; N = 10^6 on 160^2 x 1024: 1024)
+        blocks = p->gather_ctas;
+        ca.sh = 6;
+        while (ca.sh < 10 && (2 << ca.sh) <= n / p->nsm) ++ca.sh;
+        ca.nchunk = (n + (1 << ca.sh) - 1) >> ca.sh;
+        ca.nseq = std::max(1, std::min({p->nsm, ca.nchunk, kGatherChunks}));
+    }
     const Geo &g = p->geo;
     // FP64 constants applied to the FP32 sums: quadrature weight h^3, the window
     // normalisation of the gather (and of the spread when the grid is this plan's own
@@ -959,20 +1093,10 @@ void launch_gather(se1p_plan *p, int n, const void *grid, double *phi, double *f
     sc.phi = g.h * g.h * g.hz * w3 * ((flags & 4) ? w3 : 1.0);
     sc.fxy = sc.phi * 4.0 * g.xi * g.xi / g.eta * g.h;
     sc.fz = sc.phi * 4.0 * g.xi * g.xi / g.etaz * g.hz;
-    const PartRec<T> *pr = (const PartRec<T> *)p->b.parts;
-    const T *w = (const T *)p->b.wts;
-    const T *gr = (const T *)grid;
-    const int nt = 32 * warps_per_block;
-    // the x-blocked grid keeps every block row 16-byte aligned: vector loads for every P (the smallest
-    // compiled bound that holds it; 64 systems with P = 18 gathered 4x faster per point than with
-    // scalar loads)
-    if (g.P == 24) k_gather_vec<T, 24, true><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
-    else if (g.P == 16) k_gather_vec<T, 16, true><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
-    else if (g.P == 12) k_gather_vec<T, 12, true><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
-    else if (g.P < 12) k_gather_vec<T, 12, false><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
-    else if (g.P < 16) k_gather_vec<T, 16, false><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
-    else if (g.P < 24) k_gather_vec<T, 24, false><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
-    else k_gather_vec<T, 32, false><<<blocks, nt, 0, s>>>(g, n, pr, w, gr, phi, frc, flags, sc);
+    if (ca.nseq > 0) cudaMemsetAsync(p->b.gchunk, 0, sizeof(int) * (size_t)ca.nseq, s);
+    gather_kernel<T>(g.P, ca.nseq > 0)<<<blocks, 32 * kGatherWarps, 0, s>>>(g, n, (const PartRec<T> *)p->b.parts,
+                                                               (const T *)p->b.wts, (const T *)grid, phi, frc, flags,
+                                                               sc, ca);
 }
 
 void launch_vjp_combine(int n, const double *q, const double *v, const double *Eq, const double *phiv,
@@ -1002,7 +1126,18 @@ template <typename T> void launch_grid_from_double(se1p_plan *p, const double *s
     k_grid_from_user<T><<<blocks_for(n, 256, 4096), 256, 0, s>>>(p->M3, p->Mt, src, (T *)dst);
 }
 
-template <typename T> int configure_particle_kernels() { return 0; }
+// the number of CTAs of this plan's handout gather resident at once (a preference for a small
+// shared-memory carveout left room for one CTA per SM: 8 KB, 8 warps)
+template <typename T> int configure_particle_kernels(se1p_plan *p)
+{
+    const GatherKernel<T> k = gather_kernel<T>(p->geo.P, true);
+    int nsm = 0, occ = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 32 * kGatherWarps, 0) != cudaSuccess) return 1;
+    p->nsm = std::max(nsm, 1);
+    p->gather_ctas = p->nsm * std::max(occ, 1);
+    return 0;
+}
 
 template <typename T> void launch_fold(se1p_plan *p, cudaStream_t s)
 {
@@ -1025,7 +1160,7 @@ template <typename T> void launch_unfold(se1p_plan *p, cudaStream_t s)
     template void launch_gather<T>(se1p_plan *, int, const void *, double *, double *, int, cudaStream_t);  \
     template void launch_grid_to_double<T>(se1p_plan *, const void *, double *, double, cudaStream_t);           \
     template void launch_grid_from_double<T>(se1p_plan *, const double *, void *, cudaStream_t);           \
-    template int configure_particle_kernels<T>();                                                          \
+    template int configure_particle_kernels<T>(se1p_plan *);                                               \
     template void launch_fold<T>(se1p_plan *, cudaStream_t);                                                \
     template void launch_unfold<T>(se1p_plan *, cudaStream_t);
 SE1P_INST(float)

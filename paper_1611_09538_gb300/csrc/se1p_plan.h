@@ -37,6 +37,7 @@ struct Buffers {
     int *starts = nullptr;       // [nbins + 1 + ncells + 1]
     int *cursors = nullptr;      // [nbins + ncells]
     int *scan_tmp = nullptr;     // block offsets of the multi-block cell scan [kScanTmp]
+    int *gchunk = nullptr;       // [kGatherChunks] next particle of each chunk of the gather
     void *parts = nullptr;       // PartRec<T> [n_max]
     void *wts = nullptr;         // T [n_max][3][P]
     void *cells = nullptr;       // CellRec<T> [n_max]
@@ -53,6 +54,8 @@ struct Buffers {
 };
 
 constexpr int kEnergyBlocks = 256;
+// the gather's particles in at most this many contiguous chunks (one per SM)
+constexpr int kGatherChunks = 256;
 
 }  // namespace se1p
 
@@ -62,6 +65,8 @@ struct se1p_plan {
     int n_max = 0;
     int precision = 0;
     int device = 0;
+    int nsm = 1;  // SMs of the device
+    int gather_ctas = 1;  // resident CTAs of the gather kernels (SMs x CTAs per SM of the largest instance)
     int Mt = 0, M3 = 0, K3 = 0, n0 = 0, nI = 0, nl = 0;
     // free-axis size of the transformed grid: Mt for SE1P; M for triply periodic plans, whose gridding
     // runs on the Mt = M + P extended grid and is folded onto the M-periodic grid before the FFTs
@@ -110,7 +115,7 @@ void launch_finalize(se1p_plan *p, int n, double *phi, double *frc, double *ener
 template <typename T>
 void launch_grid_to_double(se1p_plan *p, const void *src, double *dst, double scale, cudaStream_t s);
 template <typename T> void launch_grid_from_double(se1p_plan *p, const double *src, void *dst, cudaStream_t s);
-template <typename T> int configure_particle_kernels();
+template <typename T> int configure_particle_kernels(se1p_plan *p);
 // triply periodic plans: fold the extended spread grid onto the periodic grid, and back
 template <typename T> void launch_fold(se1p_plan *p, cudaStream_t s);
 template <typename T> void launch_unfold(se1p_plan *p, cudaStream_t s);

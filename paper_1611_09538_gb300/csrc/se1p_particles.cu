@@ -656,8 +656,8 @@ __device__ __forceinline__ int sm_id()
 }
 
 // Particle handout of the gather, for long particle lists.  The bin-sorted particles form chunks of
-// 2^sh consecutive ones, and sequence q is made of the chunks q, q + nseq, q + 2 nseq, ... (one sequence
-// per SM).  A warp starts on the sequence of its SM, so the warps of one SM read neighbouring supports
+// cl consecutive ones, and sequence q is made of the chunks q, q + nseq, q + 2 nseq, ... (one sequence
+// per SM, all of them equally long but for the last chunk).  A warp starts on the sequence of its SM, so the warps of one SM read neighbouring supports
 // at the same time and find them in L1 (with a fixed stride over the particles, the CTAs of an SM
 // worked on unrelated parts of the grid: L1 hit rate 66 %), and all SMs move through the grid together,
 // so that the part of the grid in use stays in L2 (one contiguous chunk per SM kept the whole grid in
@@ -669,7 +669,8 @@ struct ChunkArgs {
     int *next;   // cursor of each sequence
     int nseq;    // sequences, 0: no handout (warp w takes the particles w, w + warps, ...)
     int nchunk;  // chunks
-    int sh;      // log2 of the chunk length
+    int cl;      // chunk length
+    FastDiv fcl;
     int n;
 };
 
@@ -681,7 +682,8 @@ __device__ __forceinline__ int chunk_claim(const ChunkArgs &c, const int *st, in
 // the particle of the t-th claim on sequence q (n or more once the sequence is used up)
 __device__ __forceinline__ int seq_particle(const ChunkArgs &c, int q, int t)
 {
-    return ((q + c.nseq * (t >> c.sh)) << c.sh) + (t & ((1 << c.sh) - 1));
+    const int j = fdiv(t, c.fcl);
+    return (q + c.nseq * j) * c.cl + (t - j * c.cl);
 }
 
 __device__ __forceinline__ void chunk_set(int *st, int q, int lane)
@@ -700,8 +702,8 @@ __device__ __forceinline__ int chunk_refill(const ChunkArgs &c, int *st, int lan
         for (int q = lane; q < c.nseq; q += 32) {
             // particles of sequence q: its chunks, the last chunk of the list possibly short
             const int cnt = q < c.nchunk ? (c.nchunk - 1 - q) / c.nseq + 1 : 0;
-            int len = cnt << c.sh;
-            if (cnt > 0 && (c.nchunk - 1) % c.nseq == q) len -= ((c.nchunk) << c.sh) - c.n;
+            int len = cnt * c.cl;
+            if (cnt > 0 && (c.nchunk - 1) % c.nseq == q) len -= c.nchunk * c.cl - c.n;
             const int l = len - __ldcg(c.next + q);
             if (l > left) {
                 left = l;
@@ -1062,6 +1064,10 @@ constexpr int kGatherWarps = 8;  // warps per CTA, one particle each at a time
 // one particle per warp, with no atomics (64 systems of 1000 to 50 000 particles: 15.10 against
 // 14.63 ms with every list handed out)
 constexpr int kGatherHandoutPerWarp = 16;
+// longest chunk: the SMs' chunks together make the part of the grid in use at once (N = 10^6 on
+// 160^2 x 1024 points, gather alone: power-of-two chunks of 64 / 1024 / 4096 took 3.35 / 3.22 / 3.37 ms;
+// one contiguous chunk per SM 3.52 ms, the whole grid in use and the L2 hit rate down to 62 %)
+constexpr int kGatherChunkMax = 1024;
 
 template <typename T>
 void launch_gather(se1p_plan *p, int n, const void *grid, double *phi, double *frc, int flags, cudaStream_t s)
@@ -1072,17 +1078,20 @@ void launch_gather(se1p_plan *p, int n, const void *grid, double *phi, double *f
     ca.n = n;
     ca.nseq = 0;
     ca.nchunk = 0;
-    ca.sh = 0;
+    ca.cl = 1;
     int blocks = (n + kGatherWarps - 1) / kGatherWarps;  // one particle per warp
     if ((long long)n >= (long long)kGatherHandoutPerWarp * kGatherWarps * p->gather_ctas) {
-        // as many CTAs as are resident at once; chunks of n / SMs particles rounded down to a power of
-        // two in [64, 1024] (N = 10^5 on 96^2 x 64 points: 512; N = 10^6 on 160^2 x 1024: 1024)
+        // as many CTAs as are resident at once; every sequence the same number of chunks of at most
+        // kGatherChunkMax particles (N = 10^5 on 96^2 x 64 points: one chunk of 658 per SM; N = 10^6 on
+        // 160^2 x 1024: seven of 940)
         blocks = p->gather_ctas;
-        ca.sh = 6;
-        while (ca.sh < 10 && (2 << ca.sh) <= n / p->nsm) ++ca.sh;
-        ca.nchunk = (n + (1 << ca.sh) - 1) >> ca.sh;
-        ca.nseq = std::max(1, std::min({p->nsm, ca.nchunk, kGatherChunks}));
+        const int nsq = std::min(p->nsm, kGatherChunks);
+        const int rounds = (n + nsq * kGatherChunkMax - 1) / (nsq * kGatherChunkMax);
+        ca.cl = (n + nsq * rounds - 1) / (nsq * rounds);
+        ca.nchunk = (n + ca.cl - 1) / ca.cl;
+        ca.nseq = std::min(nsq, ca.nchunk);
     }
+    ca.fcl = make_fastdiv((unsigned)ca.cl);
     const Geo &g = p->geo;
     // FP64 constants applied to the FP32 sums: quadrature weight h^3, the window
     // normalisation of the gather (and of the spread when the grid is this plan's own

@@ -37,7 +37,7 @@ struct Buffers {
     int *starts = nullptr;       // [nbins + 1 + ncells + 1]
     int *cursors = nullptr;      // [nbins + ncells]
     int *scan_tmp = nullptr;     // block offsets of the multi-block cell scan [kScanTmp]
-    int *gchunk = nullptr;       // [kGatherChunks] next particle of each chunk of the gather
+    int *gchunk = nullptr;       // [kGatherChunks] cursor of each chunk sequence of the gather's handout
     void *parts = nullptr;       // PartRec<T> [n_max]
     void *wts = nullptr;         // T [n_max][3][P]
     void *cells = nullptr;       // CellRec<T> [n_max]
@@ -54,7 +54,7 @@ struct Buffers {
 };
 
 constexpr int kEnergyBlocks = 256;
-// the gather's particles in at most this many contiguous chunks (one per SM)
+// chunk sequences of the gather's handout at most (one per SM)
 constexpr int kGatherChunks = 256;
 
 }  // namespace se1p
